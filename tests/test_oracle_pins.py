@@ -1,0 +1,433 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage of arXiv 2306.15678 (or the mathematical fact) it
+checks.  None of them compares the oracle with itself: the expected values come
+from brute force, a library routine, a closed form, an exact identity or a
+conservation law.  The last group plants a mistake in a copy of the oracle and
+checks that a pin fails.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_15678_gb300 import beams, configs
+
+RNG = np.random.default_rng(12345)
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def crand(shape, rng=RNG):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# --------------------------------------------------------------- FFT (Eq. 2)
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16])
+def test_fft2_matches_brute_force_dft(n):
+    """O(N^4) DFT written from its definition X[ky,kx] = sum a[y,x] e^{-2pi i (ky y + kx x)/N}."""
+    a = crand((n, n))
+    idx = np.arange(n)
+    expected = np.zeros((n, n), dtype=np.complex128)
+    for ky in range(n):
+        for kx in range(n):
+            ph = np.exp(-2j * np.pi * (ky * idx[:, None] + kx * idx[None, :]) / n)
+            expected[ky, kx] = np.sum(a * ph)
+    assert rel_max(oracle.fft2(a), expected) < 1e-13
+    # inverse: e^{+2pi i ...} / N^2
+    back = np.zeros_like(expected)
+    for y in range(n):
+        for x in range(n):
+            ph = np.exp(2j * np.pi * (y * idx[:, None] + x * idx[None, :]) / n)
+            back[y, x] = np.sum(a * ph) / (n * n)
+    assert rel_max(oracle.fft2(a, inverse=True), back) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 32, 64])
+def test_fft1_matches_brute_force_dft(n):
+    a = crand(n)
+    k = np.arange(n)
+    W = np.exp(-2j * np.pi * np.outer(k, k) / n)
+    assert rel_max(oracle.fft1(a), W @ a) < 1e-13
+    assert rel_max(oracle.fft1(a, inverse=True), np.conj(W) @ a / n) < 1e-13
+
+
+def test_fft2_matches_numpy_at_256():
+    a = crand((256, 256))
+    assert rel_max(oracle.fft2(a), np.fft.fft2(a)) < 1e-13
+    assert rel_max(oracle.fft2(a, inverse=True), np.fft.ifft2(a)) < 1e-13
+
+
+def test_fft2_parseval_and_roundtrip():
+    a = crand((128, 128))
+    A = oracle.fft2(a)
+    lhs = math.fsum(np.abs(A).ravel() ** 2)
+    rhs = 128 * 128 * math.fsum(np.abs(a).ravel() ** 2)
+    assert abs(lhs / rhs - 1) < 1e-14
+    assert rel_max(oracle.fft2(A, inverse=True), a) < 1e-14
+
+
+# ------------------------------------------------- diffraction (Eq. 1-2)
+
+def gaussian_closed_form(n, L, w0, A, k0, z):
+    """Gaussian beam of 2 i k0 dU/dz = Lap U (the paper's sign convention):
+    U = A/(1 - i z/zR) exp(-r^2 / (w0^2 (1 - i z/zR))), zR = k0 w0^2 / 2."""
+    x = beams.cell_centres(n, L)
+    r2 = x[:, None] ** 2 + x[None, :] ** 2
+    zR = k0 * w0 * w0 / 2.0
+    q = 1.0 - 1j * z / zR
+    return A / q * np.exp(-r2 / (w0 * w0 * q))
+
+
+def test_linear_march_matches_closed_form_gaussian():
+    """256^2, 25.6 mm window, w0 = 2 mm, 200 steps of 1 cm with diffraction only."""
+    cfg = configs.cfg_plain_fp64()
+    cfg = dict(cfg, terms=configs.DIFFRACTION)
+    b = cfg["beam"]
+    U0 = beams.gaussian_beam(cfg["n"], cfg["L"], b["w0"], b["P"])
+    U, pw, _ = oracle.march(U0, cfg, 200)
+    k0 = 2 * math.pi / cfg["lambda0"]
+    A = math.sqrt(2 * b["P"] / (math.pi * b["w0"] ** 2))
+    ref = gaussian_closed_form(cfg["n"], cfg["L"], b["w0"], A, k0, 200 * cfg["dz"])
+    assert rel_l2(U, ref) < 1e-12
+    # the opposite propagator sign gives the conjugate-convention beam, far off
+    bad = gaussian_closed_form(cfg["n"], cfg["L"], b["w0"], A, -k0, 200 * cfg["dz"])
+    assert rel_l2(U, bad) > 1e-2
+    assert np.max(np.abs(pw / pw[0] - 1)) < 1e-13
+
+
+def test_propagator_is_unimodular_and_even():
+    cfg = configs.physics(32, 1.0, 3.0, configs.DIFFRACTION)
+    P = oracle.propagator(cfg)
+    assert np.max(np.abs(np.abs(P) - 1)) < 1e-15
+    # k -> -k symmetry (index m -> N - m) in both dimensions
+    m = (-np.arange(32)) % 32
+    assert rel_max(P[m][:, m], P) < 1e-15
+    assert rel_max(P.T, P) < 1e-15
+    # phase at bin (0, 1): (2 pi / L)^2 dz / (2 k0)
+    k0 = 2 * math.pi / cfg["lambda0"]
+    expect = (2 * math.pi / cfg["L"]) ** 2 * cfg["dz"] / (2 * k0)
+    assert abs(np.angle(P[0, 1]) - (expect % (2 * math.pi) if expect < math.pi else
+                                    math.remainder(expect, 2 * math.pi))) < 1e-12
+
+
+# -------------------------------------------------- screen (Eq. 2 and Eq. 3)
+
+def field_with_intensity(n, Imax, rng):
+    return np.sqrt(Imax) * (rng.uniform(0.05, 1.0, (n, n)) *
+                            np.exp(1j * rng.uniform(-np.pi, np.pi, (n, n))))
+
+
+def test_kerr_screen_exact_phase_identity():
+    """Kerr only, no diffraction: |U_out| = |v| and arg(U_out/v) = -k0 n2 |v|^2 dz."""
+    cfg = configs.physics(32, 1.0, 0.5, configs.KERR)
+    v = field_with_intensity(32, 3e12, np.random.default_rng(1))
+    U = oracle.screen(v, cfg)
+    I = np.abs(v) ** 2
+    k0 = 2 * math.pi / cfg["lambda0"]
+    assert rel_max(np.abs(U), np.abs(v)) < 1e-15
+    phase = np.angle(U / v)
+    expect = np.angle(np.exp(-1j * k0 * cfg["n2"] * I * cfg["dz"]))
+    assert np.max(np.abs(phase - expect)) < 1e-12
+
+
+def test_screen_gain_convention_on_kerr():
+    """Complex gain c_K = theta0 + i theta1 on the Kerr screen: the imaginary part
+    turns the phase into an amplitude factor exp(theta1 k0 n2 I dz)."""
+    th = (0.7, 0.3, 1.0, 0.0, 1.0, 0.0)
+    cfg = configs.physics(16, 1.0, 0.5, configs.KERR, theta=th)
+    v = field_with_intensity(16, 1e12, np.random.default_rng(2))
+    U = oracle.screen(v, cfg)
+    I = np.abs(v) ** 2
+    a = 2 * math.pi / cfg["lambda0"] * cfg["n2"] * cfg["dz"] * I
+    assert rel_max(np.abs(U) / np.abs(v), np.exp(0.3 * a)) < 1e-14
+    assert np.max(np.abs(np.angle(U / v) - np.angle(np.exp(-1j * 0.7 * a)))) < 1e-12
+
+
+def test_plasma_screen_pure_defocusing_phase():
+    """Plasma only: |U| kept, phase +(k0 sigma_K rho_nt tau_pl / (2 rho_c)) I^K dz."""
+    cfg = configs.physics(16, 1.0, 0.5, configs.PLASMA)
+    v = field_with_intensity(16, 6e13, np.random.default_rng(3))
+    U = oracle.screen(v, cfg)
+    I = np.abs(v) ** 2
+    k0 = 2 * math.pi / cfg["lambda0"]
+    ph = k0 * cfg["sigmaK"] * cfg["rho_nt"] * cfg["tau_pl"] / (2 * cfg["rho_c"]) * I ** 8 * cfg["dz"]
+    assert ph.max() > 0.5  # the test exercises a sizeable phase
+    assert rel_max(np.abs(U), np.abs(v)) < 1e-15
+    assert np.max(np.abs(np.angle(U / v) - np.angle(np.exp(1j * ph)))) < 1e-11
+
+
+def test_mpa_screen_exact_attenuation():
+    """Absorption only: I_out = I exp(-beta_K I^(K-1) dz), phase kept."""
+    cfg = configs.physics(16, 1.0, 5.0, configs.MPA)
+    v = field_with_intensity(16, 6e13, np.random.default_rng(4))
+    U = oracle.screen(v, cfg)
+    I = np.abs(v) ** 2
+    expect = I * np.exp(-cfg["betaK"] * I ** 7 * cfg["dz"])
+    assert (expect / I).min() < 0.9
+    assert rel_max(np.abs(U) ** 2, expect) < 1e-14
+    assert np.max(np.abs(np.angle(U / v))) < 1e-14
+
+
+def test_mpa_march_converges_to_ode_closed_form():
+    """dI/dz = -beta I^K has I(z) = I0 (1 + (K-1) beta I0^(K-1) z)^(-1/(K-1)); the
+    frozen-intensity screen converges to it at first order in dz."""
+    I0, z = 1e14, 2.0
+    v = np.full((4, 4), math.sqrt(I0), dtype=np.complex128)
+    exact = I0 * (1 + 7 * configs.BETA_K * I0 ** 7 * z) ** (-1 / 7)
+    errs = []
+    for m in (40, 80, 160, 320):
+        cfg = configs.physics(4, 1.0, z / m, configs.MPA)
+        U, _, _ = oracle.march(v, cfg, m)
+        errs.append(abs(np.abs(U[0, 0]) ** 2 / exact - 1))
+    assert exact / I0 < 0.6
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in ratios), (errs, ratios)
+    assert errs[-1] < 2e-2
+
+
+# ------------------------------------------------------ march invariants
+
+def small_cfg(n, terms, nsteps, power_pcr=10.0, L=2.56, w0=0.2, dz=1.0, noise=True):
+    cfg = configs.physics(n, L, dz, terms)
+    b = dict(w0=w0, P=power_pcr * configs.critical_power(), amp=0.05 if noise else 0.0,
+             ell_cells=3.0, seed=7 if noise else None, phase=0.0, phase_seed=None)
+    cfg.update(beam=b, nsteps=nsteps)
+    return cfg
+
+
+def test_lossless_march_conserves_power():
+    """Kerr + diffraction (Eq. 1 with eps_h = 0) conserves power to rounding."""
+    cfg = small_cfg(128, configs.KERR | configs.DIFFRACTION, 100)
+    U0 = beams.make_field(cfg)
+    U, pw, pk = oracle.march(U0, cfg, 100)
+    assert pk[-1] > 1.2 * pk[0]  # self-focusing is active
+    assert np.max(np.abs(pw / pw[0] - 1)) < 1e-12
+
+
+def test_time_reversal_recovers_input():
+    """Lossless step N(dz) L(dz) is undone by L(-dz) N(-dz)."""
+    cfg = small_cfg(64, configs.KERR | configs.PLASMA | configs.DIFFRACTION, 30,
+                    power_pcr=60.0, w0=0.25)
+    U0 = beams.make_field(cfg)
+    U, _, pk = oracle.march(U0, cfg, 30)
+    back = dict(cfg, dz=-cfg["dz"])
+    for _ in range(30):
+        U = oracle.screen(U, back)
+        U = oracle.linear(U, back)
+    assert rel_l2(U, U0) < 1e-11
+
+
+def test_mpa_discrete_energy_balance():
+    """With absorption the power after a step is sum I_v exp(-beta I_v^(K-1) dz) dx^2
+    where v is the diffracted field (the linear step is unitary)."""
+    cfg = small_cfg(64, configs.ALL_TERMS, 1, power_pcr=400.0, w0=0.12, dz=2.0)
+    U = beams.make_field(cfg)
+    dx2 = (cfg["L"] / cfg["n"]) ** 2
+    lost = 0.0
+    for _ in range(6):
+        v = oracle.linear(U, cfg)
+        assert abs(oracle.power(v, cfg["L"]) / oracle.power(U, cfg["L"]) - 1) < 1e-13
+        Iv = np.abs(v) ** 2
+        expect = math.fsum((Iv * np.exp(-cfg["betaK"] * Iv ** 7 * cfg["dz"])).ravel()) * dx2
+        U, pw, _ = oracle.march(U, cfg, 1)
+        assert abs(pw[1] / expect - 1) < 1e-13
+        lost = max(lost, 1 - pw[1] / pw[0])
+    assert lost > 1e-6  # absorption is active in this case
+
+
+def test_radial_beam_keeps_mirror_and_transpose_symmetry():
+    """A radially symmetric input stays symmetric under x<->y and x -> -x (cell-centred
+    grid: j -> N-1-j).  Checked before the collapse, where rounding asymmetries
+    are not yet amplified (they grow to 1e-10 within ten more steps)."""
+    cfg = small_cfg(64, configs.ALL_TERMS, 4, power_pcr=200.0, w0=0.25, dz=20.0, noise=False)
+    U0 = beams.make_field(cfg)
+    U, _, pk = oracle.march(U0, cfg, 4)
+    assert pk[-1] > 2 * pk[0]
+    scale = np.max(np.abs(U))
+    assert np.max(np.abs(U - U.T)) / scale < 1e-12
+    assert np.max(np.abs(U - U[::-1, :])) / scale < 1e-12
+    assert np.max(np.abs(U - U[:, ::-1])) / scale < 1e-12
+
+
+def test_linear_operator_adjoint_dot_product():
+    """<L a, b> = <a, L^H b> with L^H = IFFT2 conj(P) FFT2 = L(-dz)."""
+    cfg = configs.physics(32, 1.0, 7.0, configs.DIFFRACTION)
+    rng = np.random.default_rng(5)
+    a, b = crand((32, 32), rng), crand((32, 32), rng)
+    lhs = np.vdot(oracle.linear(a, cfg), b)
+    rhs = np.vdot(a, oracle.linear(b, dict(cfg, dz=-cfg["dz"])))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-13
+
+
+# --------------------------------------------------------------- readouts
+
+def test_power_peak_fluence_loss():
+    rng = np.random.default_rng(6)
+    U = crand((64, 64), rng) * 1e5
+    L = 3.2
+    dx2 = (L / 64) ** 2
+    assert abs(oracle.power(U, L) / (math.fsum((np.abs(U) ** 2).ravel()) * dx2) - 1) < 1e-15
+    assert oracle.peak(U) == pytest.approx(float(np.max(np.abs(U) ** 2)), rel=1e-15)
+    F8 = oracle.fluence(U, 8)
+    brute = np.zeros((8, 8))
+    for R in range(8):
+        for C in range(8):
+            brute[R, C] = sum(abs(U[R * 8 + r, C * 8 + c]) ** 2
+                              for r in range(8) for c in range(8)) / 64
+    assert rel_max(F8, brute) < 1e-14
+    D = np.abs(crand((64, 64), rng)) ** 2
+    assert oracle.loss(np.sqrt(D), D) < 1e-28
+    assert oracle.loss(np.zeros((64, 64)), D) == pytest.approx(1.0, rel=1e-14)
+    Us = crand((4, 4), rng)
+    Ds = np.abs(crand((4, 4), rng))
+    num = sum((abs(Us[i, j]) ** 2 - Ds[i, j]) ** 2 for i in range(4) for j in range(4))
+    den = sum(Ds[i, j] ** 2 for i in range(4) for j in range(4))
+    assert oracle.loss(Us, Ds) == pytest.approx(num / den, rel=1e-14)
+
+
+# ---------------------------------------------------------------- adjoint
+
+def adjoint_case():
+    cfg = small_cfg(32, configs.ALL_TERMS, 12, power_pcr=300.0, L=1.6, w0=0.12, dz=3.0)
+    U0 = beams.make_field(cfg)
+    other = small_cfg(32, configs.ALL_TERMS, 12, power_pcr=250.0, L=1.6, w0=0.14, dz=3.0)
+    D = np.abs(beams.make_field(other)) ** 2
+    return cfg, U0, D
+
+
+def loss_of(cfg, U0, D, nsteps):
+    U, _, _ = oracle.march(U0, cfg, nsteps, record=False)
+    return oracle.loss(U, D)
+
+
+def test_adjoint_theta_gradient_matches_central_differences():
+    cfg, U0, D = adjoint_case()
+    J, dth, _ = oracle.adjoint(U0, D, cfg, 12, ckpt=5)
+    _, _, pk = oracle.march(U0, cfg, 12)
+    assert pk.max() > 2e13  # plasma and absorption matter along this path
+    assert J == pytest.approx(loss_of(cfg, U0, D, 12), rel=1e-14)
+    def central(j, h):
+        tp = list(cfg["theta"]); tp[j] += h
+        tm = list(cfg["theta"]); tm[j] -= h
+        return (loss_of(dict(cfg, theta=tuple(tp)), U0, D, 12) -
+                loss_of(dict(cfg, theta=tuple(tm)), U0, D, 12)) / (2 * h)
+
+    h = 1e-4
+    for j in range(6):
+        # central differences at h and h/2, Richardson-extrapolated (error O(h^4))
+        fd = (4 * central(j, h / 2) - central(j, h)) / 3
+        assert abs(dth[j] - fd) <= 1e-7 * max(abs(fd), 1e-3 * np.max(np.abs(dth))), (j, dth[j], fd)
+
+
+def test_adjoint_field_gradient_matches_directional_difference():
+    cfg, U0, D = adjoint_case()
+    _, _, dU0 = oracle.adjoint(U0, D, cfg, 12, ckpt=4)
+    rng = np.random.default_rng(8)
+    for _ in range(2):
+        d = crand(U0.shape, rng) * np.abs(U0).max()
+        def central(h):
+            return (loss_of(cfg, U0 + h * d, D, 12) - loss_of(cfg, U0 - h * d, D, 12)) / (2 * h)
+        h = 2e-5
+        fd = (4 * central(h / 2) - central(h)) / 3
+        an = float(np.real(np.vdot(dU0, d)))
+        assert abs(an - fd) < 1e-7 * abs(fd), (an, fd)
+
+
+def test_adjoint_independent_of_checkpoint_spacing():
+    cfg, U0, D = adjoint_case()
+    J1, t1, g1 = oracle.adjoint(U0, D, cfg, 12, ckpt=1)
+    J2, t2, g2 = oracle.adjoint(U0, D, cfg, 12, ckpt=7)
+    assert J1 == J2
+    assert np.array_equal(t1, t2)
+    assert np.array_equal(g1, g2)
+
+
+# ------------------------------------------- printed constants (golden file)
+
+def golden():
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "printed_constants.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+def test_critical_power_reproduces_printed_ratio():
+    """380 GW = 112 Pcr (Sec. 3.2) is lambda^2/(2 pi n0 n2) at n2 = 3.0e-19."""
+    g = golden()
+    pcr = configs.critical_power(g["lambda0_cm"], 1.0, 3.0e-19)
+    assert pcr == pytest.approx(g["P0_W"] / g["P0_over_Pcr"], rel=2e-3)
+    # at the build's n2 = 3.2e-19 the value stays near the 4-7 GW range quoted in Sec. 2
+    assert 0.75 * g["Pcr_low_W"] < configs.critical_power() < g["Pcr_high_W"]
+
+
+def test_pulse_duration_and_thresholds_from_printed_values():
+    g = golden()
+    assert configs.TAU_PL == pytest.approx(g["pulse_energy_J"] / g["peak_power_W"], rel=1e-12)
+    assert configs.W_PF == g["wpf_low_Wcm2"]
+    assert configs.LAMBDA0 == g["lambda0_cm"]
+
+
+# --------------------------------------------------------- input generator
+
+def test_input_generator_power_and_noise_statistics():
+    b = configs.cfg_plain_fp64()["beam"]
+    U = beams.gaussian_beam(256, 2.56, b["w0"], b["P"])
+    dx2 = (2.56 / 256) ** 2
+    assert math.fsum((np.abs(U) ** 2).ravel()) * dx2 == pytest.approx(b["P"], rel=1e-12)
+    eta = beams.smoothed_noise(128, 4.0, 1)
+    assert abs(eta.mean()) < 1e-12 and abs(eta.std() - 1) < 1e-12
+    assert np.array_equal(eta, beams.smoothed_noise(128, 4.0, 1))
+    # correlation: neighbouring cells strongly correlated at l = 4 cells
+    c = np.mean(eta * np.roll(eta, 1, axis=1))
+    assert c > 0.8
+
+
+# ------------------------------------------------ planted mistakes (CPU)
+
+MUTANTS = [
+    # (name, original text, replacement, pin that must fail)
+    ("propagator sign", "P[(size_t)r * n + c] = cexp(I * phase);",
+     "P[(size_t)r * n + c] = cexp(-I * phase);", "gauss"),
+    ("Nyquist / negative frequency index", "int mm = (m < n / 2) ? m : m - n;",
+     "int mm = m;", "gauss"),
+    ("Kerr factor 2 dropped", "c.eps_k = 2.0 * c.k0 * c.k0 * p->n2 / p->n0;",
+     "c.eps_k = c.k0 * c.k0 * p->n2 / p->n0;", "kerr"),
+    ("absorption exponent K instead of K-1",
+     "bracket += c->cA * I * c->k0 * c->alpha_m * pow(In, (double)(p->K - 1));",
+     "bracket += c->cA * I * c->k0 * c->alpha_m * pow(In, (double)(p->K));", "mpa"),
+    ("transposed column pass", "for (int r = 0; r < n; ++r) col[r] = a[(size_t)r * n + c];",
+     "for (int r = 0; r < n; ++r) col[r] = a[(size_t)c * n + r];", "fft"),
+    ("adjoint screen conj dropped", "G[i] = conj(e) * gw + 2.0",
+     "G[i] = e * gw + 2.0", "adjoint"),
+]
+
+
+@pytest.mark.parametrize("name,orig,repl,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch):
+    src = oracle.source_text()
+    assert orig in src, name
+    lib = oracle.compile_variant(src.replace(orig, repl), str(tmp_path / "mutant.so"))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    pins = {
+        "gauss": test_linear_march_matches_closed_form_gaussian,
+        "kerr": test_kerr_screen_exact_phase_identity,
+        "mpa": test_mpa_screen_exact_attenuation,
+        "fft": lambda: test_fft2_matches_brute_force_dft(8),
+        "adjoint": test_adjoint_field_gradient_matches_directional_difference,
+    }
+    with pytest.raises(AssertionError):
+        pins[pin]()
