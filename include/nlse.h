@@ -1,0 +1,183 @@
+/*
+ * nlse.h -- C ABI of the GB300 (sm_103a) split-step Fourier march of the
+ * stationary transverse nonlinear Schroedinger equation (NLSE) of
+ * Bulygin & Geints, arXiv 2306.15678.
+ *
+ * The method (Sec. 2):
+ *   Eq. 1   2 i k0 dU/dz = (Lap_perp + eps_k U U* + eps_h[U]) U
+ *   Eq. 3   eps_h U = (eps_m (UU*)^K + i k0 alpha_m (UU*)^(K-1)) U
+ *           (the printed exponents 2m and 2(m-1) are read as m = K and K-1:
+ *           plasma refraction ~ I^K, K-photon absorption ~ I^(K-1) in the field
+ *           equation, i.e. dI/dz = -beta_K I^K)
+ *   Eq. 2   one z step is the operator exponential split into diffraction
+ *           exp(i k_perp^2 dz / (2 k0)) applied in Fourier space and a pointwise
+ *           complex phase screen evaluated on the field entering the screen.
+ *
+ * One call of nlse_step(g, n) advances the field by n Lie steps
+ *   U <- v exp(s(|v|^2)),   v = IFFT2( exp(i (kx^2+ky^2) dz/(2 k0)) FFT2(U) ),
+ *   s(I) = -i dz/(2 k0) [c_K eps_k I + c_P eps_m I^K + c_A i k0 alpha_m I^(K-1)],
+ * with eps_k = 2 k0^2 n2/n0, eps_m = -k0^2 sigma_K rho_nt tau_pl / rho_c,
+ * alpha_m = -beta_K, k0 = 2 pi n0 / lambda0 and complex gains
+ * c_K = theta[0] + i theta[1], c_P = theta[2] + i theta[3],
+ * c_A = theta[4] + i theta[5] (nominal 1, 0, 1, 0, 1, 0).
+ *
+ * Units: CGS-optical.  Lengths in cm, |U|^2 in W/cm^2, power in W.
+ * Field layout everywhere: row-major n x n (row = y, column = x), complex
+ * values interleaved (re, im); complex128 for NLSE_FP64 grids, complex64 for
+ * NLSE_FP32 grids.  Grid points sit on cell centres x_j = (j - n/2 + 1/2) L/n.
+ *
+ * Memory ownership: the caller owns every device buffer (the workspace holds
+ * the field, the propagator and twiddle tables, reduction partials, the
+ * diagnostics history and the adjoint's checkpoints) and the CUDA stream.  The
+ * library owns only the opaque host structures it allocates in *_create and
+ * frees in *_destroy.  A workspace must outlive its handle and must not be
+ * shared by two live handles.
+ *
+ * Errors: every call returns an nlse_status and never aborts, traps or exits.
+ * Arguments are validated before any launch (NLSE_EINVAL, NLSE_EUNSUPPORTED,
+ * NLSE_ENOMEM for a workspace that is too small).  Launch failures and
+ * asynchronous faults surface as NLSE_ECUDA at the next call that checks
+ * them.  A device status word records non-finite readouts (NLSE_ENONFINITE)
+ * and bounded waits that ran out (NLSE_ETIMEOUT); calls that synchronise
+ * report it.
+ *
+ * Threading: a handle is bound to the stream given at creation and is not
+ * thread-safe; use one handle per host thread.  Calls that do not say
+ * "synchronises" only enqueue work on the stream.
+ */
+#ifndef NLSE_H
+#define NLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nlse_status {
+    NLSE_OK = 0,
+    NLSE_EINVAL = 1,        /* bad argument (null pointer, bad size, bad value) */
+    NLSE_EUNSUPPORTED = 2,  /* valid request outside what this build supports */
+    NLSE_ENOMEM = 3,        /* caller's workspace is smaller than required */
+    NLSE_ECUDA = 4,         /* a CUDA call or kernel launch failed */
+    NLSE_ENONFINITE = 5,    /* a readout found NaN or Inf in the field */
+    NLSE_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
+    NLSE_ESTATE = 7         /* call out of order (e.g. step before load) */
+} nlse_status;
+
+/* terms of Eq. 1-3 (bit mask) */
+enum {
+    NLSE_KERR = 1u,         /* eps_k |U|^2: Kerr self-focusing */
+    NLSE_PLASMA = 2u,       /* eps_m |U|^(2K): plasma defocusing */
+    NLSE_MPA = 4u,          /* i k0 alpha_m |U|^(2K-2): multiphoton absorption */
+    NLSE_DIFFRACTION = 8u,  /* Lap_perp */
+    NLSE_ALL_TERMS = 15u
+};
+
+/* arithmetic of the field march; reductions, tables and losses are FP64 in both */
+enum { NLSE_FP64 = 0, NLSE_FP32 = 1 };
+
+/* Physical description of one grid (Eq. 1-3, Eq. 7).  Plain old data. */
+typedef struct nlse_params {
+    int32_t n;            /* points per side: power of two, 8 <= n <= 8192 */
+    int32_t K;            /* multiphoton order (Eq. 3 "m"), 1 <= K <= 16 */
+    uint32_t terms;       /* NLSE_KERR | NLSE_PLASMA | NLSE_MPA | NLSE_DIFFRACTION */
+    int32_t precision;    /* NLSE_FP64 or NLSE_FP32 */
+    double L;             /* transverse window side, cm (> 0) */
+    double dz;            /* z step, cm (non-zero; negative marches backwards) */
+    double lambda0;       /* carrier wavelength, cm */
+    double n0;            /* linear refractive index */
+    double n2;            /* Kerr index, cm^2/W */
+    double sigmaK;        /* K-photon ionisation coefficient, s^-1 cm^(2K) W^-K */
+    double rho_nt;        /* neutral density, cm^-3 */
+    double rho_c;         /* critical plasma density, cm^-3 */
+    double tau_pl;        /* effective pulse duration, s */
+    double betaK;         /* K-photon absorption coefficient, cm^(2K-3) W^(1-K) */
+    double theta[6];      /* complex screen gains (re, im) for Kerr, plasma, absorption */
+    int32_t diag_every;   /* record power and peak every this many steps (0 = never) */
+    int32_t reserved;     /* must be 0 */
+} nlse_params;
+
+typedef struct nlse_grid nlse_grid;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* nlse_status_string(nlse_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t nlse_version(void);
+
+/* Bytes of device workspace nlse_create needs for these parameters
+ * (field, scratch field, tables, partials, history).  No CUDA call. */
+nlse_status nlse_workspace_size(const nlse_params* p, size_t* bytes);
+
+/* Create a grid on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream); `dev_workspace` is a device pointer of at
+ * least nlse_workspace_size() bytes, 256-byte aligned.  Builds the propagator
+ * tables P(kx), P(ky) (phase k^2 dz/(2 k0) in FP64, reduced mod 2 pi, then
+ * rounded to the grid precision) and the FFT twiddles on the host and copies
+ * them into the workspace (asynchronously, on the stream).  *out receives the
+ * handle.  Eq. 1-2 (propagator), Eq. 3 (screen coefficients). */
+nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_workspace,
+                        size_t workspace_bytes, nlse_grid** out);
+
+/* Load the field U (n x n interleaved complex of the grid precision; host
+ * memory if src_on_device == 0, device memory otherwise) and reset the step
+ * counter and the diagnostics history.  Eq. 7 supplies the usual initial
+ * beams (see the Python helper paper_2306_15678_gb300.beams). */
+nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device);
+
+/* Advance the field by nsteps >= 0 Lie steps (Eq. 2), asynchronously on the
+ * grid's stream: per step one column pass (FFT_y, multiply by
+ * exp(i (kx^2+ky^2) dz/(2k0))/n^2, inverse FFT_y) and one row pass (inverse
+ * FFT_x, nonlinear screen, forward FFT_x).  Every diag_every steps the row pass
+ * also reduces power and peak into the history. */
+nlse_status nlse_step(nlse_grid* g, int32_t nsteps);
+
+/* Same work as nlse_step, with CUDA events recorded on the grid's stream
+ * around every launch: adds the summed durations (milliseconds) of the column
+ * passes to *col_ms and of the row passes (with their diagnostics reduction)
+ * to *row_ms.  Either pointer may be NULL.  Synchronises.  Measurement aid
+ * for the per-kernel roofline; the paper has no counterpart. */
+nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double* row_ms);
+
+/* Number of z steps taken since the last load. */
+nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps);
+
+/* Beam power P = sum |U|^2 dx^2 in W, summed in FP64 in a fixed order
+ * (deterministic).  Synchronises the stream.  Sec. 3.1 "total pulse energy". */
+nlse_status nlse_power(nlse_grid* g, double* watts);
+
+/* Peak intensity max |U|^2 in W/cm^2.  Synchronises.  Sec. 3.1 "I_m". */
+nlse_status nlse_peak(nlse_grid* g, double* w_per_cm2);
+
+/* Fluence w = U U* (Sec. 2, before Eq. 4; stationary model), averaged over
+ * aligned downsample x downsample blocks (downsample = 1, 2, 4, ... <= n),
+ * written as (n/downsample)^2 reals of the grid precision (float for FP32,
+ * double for FP64) to dst (host if dst_on_device == 0).  Synchronises when dst
+ * is on the host. */
+nlse_status nlse_fluence(nlse_grid* g, void* dst, int dst_on_device, int downsample);
+
+/* Copy the current field U (n x n interleaved complex of the grid precision)
+ * to dst (host if dst_on_device == 0).  Synchronises when dst is on the host. */
+nlse_status nlse_read_field(nlse_grid* g, void* dst, int dst_on_device);
+
+/* Copy up to `capacity` recorded (power, peak) pairs, oldest first, into
+ * power[] and peak[] (host arrays; either may be NULL) and their count into
+ * *count.  Entry i was recorded after (i+1)*diag_every steps.  The history
+ * keeps the last 4096 records.  Synchronises. */
+nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capacity,
+                         int32_t* count);
+
+/* Read and clear the device status word (synchronises): NLSE_OK,
+ * NLSE_ENONFINITE or NLSE_ETIMEOUT. */
+nlse_status nlse_device_status(nlse_grid* g);
+
+/* Release the handle (not the caller's workspace).  Synchronises. */
+nlse_status nlse_destroy(nlse_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLSE_H */

@@ -1,0 +1,178 @@
+"""ctypes binding of the C ABI in include/nlse.h (same names, argument
+marshalling only).  Every computation happens in libnlse.so's CUDA kernels;
+when the library is missing or fails to load, every call raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnlse.so")
+
+NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
+NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
+NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15
+NLSE_FP64, NLSE_FP32 = 0, 1
+
+
+class nlse_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("terms", ctypes.c_uint32),
+        ("precision", ctypes.c_int32),
+        ("L", ctypes.c_double),
+        ("dz", ctypes.c_double),
+        ("lambda0", ctypes.c_double),
+        ("n0", ctypes.c_double),
+        ("n2", ctypes.c_double),
+        ("sigmaK", ctypes.c_double),
+        ("rho_nt", ctypes.c_double),
+        ("rho_c", ctypes.c_double),
+        ("tau_pl", ctypes.c_double),
+        ("betaK", ctypes.c_double),
+        ("theta", ctypes.c_double * 6),
+        ("diag_every", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class NlseError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {nlse_status_string(status)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    # name: (restype, argtypes)
+    "nlse_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "nlse_version": (ctypes.c_int32, []),
+    "nlse_workspace_size": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "nlse_create": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "nlse_load_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "nlse_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "nlse_steps_taken": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "nlse_power": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "nlse_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "nlse_fluence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "nlse_read_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]),
+    "nlse_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libnlse.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libnlse.so not found at {LIB_PATH}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def check(status: int, where: str) -> None:
+    if status != NLSE_OK:
+        raise NlseError(status, where)
+
+
+def nlse_status_string(status: int) -> str:
+    return lib().nlse_status_string(int(status)).decode()
+
+
+def nlse_version() -> int:
+    return int(lib().nlse_version())
+
+
+def nlse_workspace_size(p: nlse_params) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().nlse_workspace_size(ctypes.byref(p), ctypes.byref(b)), "nlse_workspace_size")
+    return int(b.value)
+
+
+def nlse_create(p: nlse_params, stream: int, workspace: int, nbytes: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    check(lib().nlse_create(ctypes.byref(p), ctypes.c_void_p(stream), ctypes.c_void_p(workspace),
+                            ctypes.c_size_t(nbytes), ctypes.byref(h)), "nlse_create")
+    return h
+
+
+def nlse_load_field(h, src: int, on_device: bool) -> None:
+    check(lib().nlse_load_field(h, ctypes.c_void_p(src), int(bool(on_device))), "nlse_load_field")
+
+
+def nlse_step(h, nsteps: int) -> None:
+    check(lib().nlse_step(h, int(nsteps)), "nlse_step")
+
+
+def nlse_step_timed(h, nsteps: int) -> tuple[float, float]:
+    """Step and return the summed (column-pass, row-pass) durations in ms."""
+    c = ctypes.c_double(0.0)
+    r = ctypes.c_double(0.0)
+    check(lib().nlse_step_timed(h, int(nsteps), ctypes.byref(c), ctypes.byref(r)), "nlse_step_timed")
+    return float(c.value), float(r.value)
+
+
+def nlse_steps_taken(h) -> int:
+    v = ctypes.c_int64(0)
+    check(lib().nlse_steps_taken(h, ctypes.byref(v)), "nlse_steps_taken")
+    return int(v.value)
+
+
+def nlse_power(h) -> float:
+    v = ctypes.c_double(0)
+    check(lib().nlse_power(h, ctypes.byref(v)), "nlse_power")
+    return float(v.value)
+
+
+def nlse_peak(h) -> float:
+    v = ctypes.c_double(0)
+    check(lib().nlse_peak(h, ctypes.byref(v)), "nlse_peak")
+    return float(v.value)
+
+
+def nlse_fluence(h, dst: int, on_device: bool, downsample: int) -> None:
+    check(lib().nlse_fluence(h, ctypes.c_void_p(dst), int(bool(on_device)), int(downsample)),
+          "nlse_fluence")
+
+
+def nlse_read_field(h, dst: int, on_device: bool) -> None:
+    check(lib().nlse_read_field(h, ctypes.c_void_p(dst), int(bool(on_device))), "nlse_read_field")
+
+
+def nlse_history(h, power_ptr: int, peak_ptr: int, capacity: int) -> int:
+    c = ctypes.c_int32(0)
+    check(lib().nlse_history(h, ctypes.c_void_p(power_ptr), ctypes.c_void_p(peak_ptr),
+                             int(capacity), ctypes.byref(c)), "nlse_history")
+    return int(c.value)
+
+
+def nlse_device_status(h) -> int:
+    return int(lib().nlse_device_status(h))
+
+
+def nlse_destroy(h) -> None:
+    check(lib().nlse_destroy(h), "nlse_destroy")

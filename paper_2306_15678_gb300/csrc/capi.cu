@@ -1,0 +1,546 @@
+// capi.cu -- host implementation of the C ABI declared in include/nlse.h:
+// parameter validation, FP64 construction of the propagator, twiddle and
+// screen tables (arXiv 2306.15678, Eq. 1-3), workspace carving, and the launch
+// sequence of the split-step march (Eq. 2).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/nlse.h"
+#include "dispatch.cuh"
+
+using namespace nlse;
+
+namespace {
+
+constexpr int kHistCap = 4096;
+constexpr double kIref = 1.0e13;  // W/cm^2: scale of the screen's intensity variable
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int log2_exact(int n) {
+    if (n <= 0 || (n & (n - 1))) return -1;
+    int k = 0;
+    while ((1 << k) < n) ++k;
+    return k;
+}
+
+struct Layout {
+    size_t state, aux, tw, px, py, partials, hist, readout, status, total;
+};
+
+Layout layout_for(int n, int precision) {
+    const size_t cs = precision == NLSE_FP64 ? 16 : 8;
+    const size_t nn = (size_t)n * n;
+    Layout L;
+    size_t o = 0;
+    L.state = o;    o = align256(o + nn * cs);
+    L.aux = o;      o = align256(o + nn * cs);
+    // table entries are 16 bytes in both precisions (FP32: hi/lo pairs)
+    L.tw = o;       o = align256(o + (size_t)n * 16);
+    L.px = o;       o = align256(o + (size_t)n * 16);
+    L.py = o;       o = align256(o + (size_t)n * 16);
+    L.partials = o; o = align256(o + (size_t)n * 2 * sizeof(double));
+    L.hist = o;     o = align256(o + (size_t)kHistCap * 2 * sizeof(double));
+    L.readout = o;  o = align256(o + 2 * sizeof(double));
+    L.status = o;   o = align256(o + sizeof(int));
+    L.total = o;
+    return L;
+}
+
+nlse_status validate(const nlse_params* p) {
+    if (!p) return NLSE_EINVAL;
+    const int k = log2_exact(p->n);
+    if (k < 0) return NLSE_EINVAL;
+    if (k < 3 || k > 13) return NLSE_EUNSUPPORTED;
+    if (p->precision != NLSE_FP64 && p->precision != NLSE_FP32) return NLSE_EUNSUPPORTED;
+    if (p->K < 1 || p->K > 16) return NLSE_EINVAL;
+    if ((p->terms & ~15u) != 0) return NLSE_EINVAL;
+    if (!(p->L > 0.0) || !std::isfinite(p->L)) return NLSE_EINVAL;
+    if (p->dz == 0.0 || !std::isfinite(p->dz)) return NLSE_EINVAL;
+    if (!(p->lambda0 > 0.0) || !(p->n0 > 0.0)) return NLSE_EINVAL;
+    const double vals[] = {p->n2, p->sigmaK, p->rho_nt, p->rho_c, p->tau_pl, p->betaK};
+    for (double v : vals)
+        if (!std::isfinite(v)) return NLSE_EINVAL;
+    if ((p->terms & NLSE_PLASMA) && !(p->rho_c > 0.0)) return NLSE_EINVAL;
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(p->theta[i])) return NLSE_EINVAL;
+    if (p->diag_every < 0 || p->reserved != 0) return NLSE_EINVAL;
+    return NLSE_OK;
+}
+
+// signed frequency index of FFT bin m
+inline double signed_bin(int m, int n) { return (double)(m < n / 2 ? m : m - n); }
+
+// Separable diffraction tables (Eq. 1-2, Lap_perp -> -(kx^2 + ky^2)):
+// P_x(m) = exp(i k_m^2 dz / (2 k0)), P_y(m) = the same divided by n^2 (the
+// normalisation of the inverse 2D transform).  Phases in FP64, reduced mod 2 pi.
+void propagator_tables(const nlse_params* p, std::vector<double>& px, std::vector<double>& py) {
+    const int n = p->n;
+    const double k0 = kTwoPi * p->n0 / p->lambda0;
+    const double inv_n2 = 1.0 / ((double)n * (double)n);
+    const bool diffr = (p->terms & NLSE_DIFFRACTION) != 0;
+    px.resize(2 * (size_t)n);
+    py.resize(2 * (size_t)n);
+    for (int m = 0; m < n; ++m) {
+        const double k = kTwoPi * signed_bin(m, n) / p->L;
+        double ph = diffr ? std::fmod(k * k * p->dz / (2.0 * k0), kTwoPi) : 0.0;
+        const double c = std::cos(ph), s = std::sin(ph);
+        px[2 * m] = c;
+        px[2 * m + 1] = s;
+        py[2 * m] = c * inv_n2;
+        py[2 * m + 1] = s * inv_n2;
+    }
+}
+
+// Twiddles W_n^i = exp(-2 pi i i / n), i < n, in FP64.
+void twiddle_table(int n, std::vector<double>& tw) {
+    tw.resize(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        // exact octant symmetry keeps |W| and the table's symmetries exact after rounding
+        const double a = kTwoPi * (double)i / (double)n;
+        tw[2 * i] = std::cos(a);
+        tw[2 * i + 1] = -std::sin(a);
+    }
+    // exact values on the axes
+    for (int i = 0; i < n; i += (n >= 4 ? n / 4 : n)) {
+        const int q = (int)((4LL * i) / n);
+        const double cq[4] = {1.0, 0.0, -1.0, 0.0}, sq[4] = {0.0, -1.0, 0.0, 1.0};
+        tw[2 * i] = cq[q & 3];
+        tw[2 * i + 1] = sq[q & 3];
+    }
+}
+
+// Screen coefficients (Eq. 2-3) in u = I / I_ref:
+//   s = -i dz/(2 k0) [c_K eps_k I + c_P eps_m I^K + c_A i k0 alpha_m I^(K-1)]
+//     = -i c_K a_K u + (-i c_P a_P) u^K + c_A a_A u^(K-1)
+// with a_K = dz eps_k/(2 k0) I_ref, a_P = dz eps_m/(2 k0) I_ref^K,
+// a_A = dz alpha_m/2 I_ref^(K-1).
+template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
+    const double k0 = kTwoPi * p->n0 / p->lambda0;
+    const double eps_k = 2.0 * k0 * k0 * p->n2 / p->n0;
+    const double eps_m = -k0 * k0 * p->sigmaK * p->rho_nt * p->tau_pl / p->rho_c;
+    const double alpha_m = -p->betaK;
+    const double aK = (p->terms & NLSE_KERR) ? p->dz * eps_k / (2.0 * k0) * kIref : 0.0;
+    const double aP = (p->terms & NLSE_PLASMA)
+                          ? p->dz * eps_m / (2.0 * k0) * std::pow(kIref, (double)p->K)
+                          : 0.0;
+    const double aA = (p->terms & NLSE_MPA)
+                          ? p->dz * alpha_m / 2.0 * std::pow(kIref, (double)(p->K - 1))
+                          : 0.0;
+    const double* th = p->theta;
+    ScreenCoef<T> c;
+    c.inv_iref = (T)(1.0 / kIref);
+    // -i (t0 + i t1) a = t1 a - i t0 a
+    c.re_k = (T)(th[1] * aK);
+    c.im_k = (T)(-th[0] * aK);
+    c.re_p = (T)(th[3] * aP);
+    c.im_p = (T)(-th[2] * aP);
+    // (t4 + i t5) a
+    c.re_a = (T)(th[4] * aA);
+    c.im_a = (T)(th[5] * aA);
+    c.K = p->K;
+    c.active = (p->terms & (NLSE_KERR | NLSE_PLASMA | NLSE_MPA)) ? 1 : 0;
+    return c;
+}
+
+// FP64 complex table -> device entries: FP32 hi/lo pairs (re_hi, im_hi, re_lo, im_lo)
+// so that each factor is exact to O(eps^2), or the FP64 values themselves
+template <typename T> void round_table(const std::vector<double>& in, std::vector<T>& out);
+template <> void round_table<double>(const std::vector<double>& in, std::vector<double>& out) {
+    out = in;
+}
+template <> void round_table<float>(const std::vector<double>& in, std::vector<float>& out) {
+    const size_t n = in.size() / 2;
+    out.resize(4 * n);
+    for (size_t i = 0; i < n; ++i) {
+        const float hr = (float)in[2 * i], hi = (float)in[2 * i + 1];
+        out[4 * i] = hr;
+        out[4 * i + 1] = hi;
+        out[4 * i + 2] = (float)(in[2 * i] - (double)hr);
+        out[4 * i + 3] = (float)(in[2 * i + 1] - (double)hi);
+    }
+}
+
+}  // namespace
+
+struct nlse_grid {
+    nlse_params p;
+    cudaStream_t stream;
+    int device;
+    unsigned char* ws;
+    Layout lay;
+    int64_t steps;
+    int64_t hist_count;
+    int loaded;
+    int cols;  // column tile of the column pass
+    const KernelSet<float>* k32;
+    const KernelSet<double>* k64;
+    ScreenCoef<float> sc32;
+    ScreenCoef<double> sc64;
+};
+
+namespace {
+
+inline nlse_status cuerr(cudaError_t e) { return e == cudaSuccess ? NLSE_OK : NLSE_ECUDA; }
+
+template <typename T> struct Sel;
+template <> struct Sel<float> {
+    static const KernelSet<float>* ks(const nlse_grid* g) { return g->k32; }
+    static const ScreenCoef<float>& sc(const nlse_grid* g) { return g->sc32; }
+};
+template <> struct Sel<double> {
+    static const KernelSet<double>* ks(const nlse_grid* g) { return g->k64; }
+    static const ScreenCoef<double>& sc(const nlse_grid* g) { return g->sc64; }
+};
+
+template <typename T> using VT = typename vec2<T>::type;
+template <typename T> using WT = typename tab_of<T>::type;
+template <typename T> const WT<T>* tab(nlse_grid* g, size_t off) {
+    return reinterpret_cast<const WT<T>*>(g->ws + off);
+}
+
+template <typename T> VT<T>* at(nlse_grid* g, size_t off) { return reinterpret_cast<VT<T>*>(g->ws + off); }
+inline double* dat(nlse_grid* g, size_t off) { return reinterpret_cast<double*>(g->ws + off); }
+
+template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_t* ev = nullptr) {
+    const KernelSet<T>* ks = Sel<T>::ks(g);
+    VT<T>* field = at<T>(g, g->lay.state);
+    const WT<T>* tw = tab<T>(g, g->lay.tw);
+    const WT<T>* px = tab<T>(g, g->lay.px);
+    const WT<T>* py = tab<T>(g, g->lay.py);
+    double* partials = dat(g, g->lay.partials);
+    const double dx = g->p.L / g->p.n;
+    for (int s = 0; s < nsteps; ++s) {
+        if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
+        cudaError_t e = ks->col_pass(field, tw, px, py, g->cols, g->stream);
+        if (e != cudaSuccess) return NLSE_ECUDA;
+        if (ev && cudaEventRecord(ev[2 * s + 1], g->stream) != cudaSuccess) return NLSE_ECUDA;
+        const bool diag = g->p.diag_every > 0 && ((g->steps + 1) % g->p.diag_every) == 0;
+        e = ks->row_pass(field, tw, Sel<T>::sc(g), partials, diag, g->stream);
+        if (e != cudaSuccess) return NLSE_ECUDA;
+        if (diag) {
+            double* slot = dat(g, g->lay.hist) + 2 * (g->hist_count % kHistCap);
+            k_finalize<<<1, 256, 0, g->stream>>>(partials, ks->row_blocks, dx * dx, slot,
+                                                 reinterpret_cast<int*>(g->ws + g->lay.status));
+            if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+            ++g->hist_count;
+        }
+        if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
+        ++g->steps;
+    }
+    return NLSE_OK;
+}
+
+// readout of the current field: optional field/fluence output; (power, peak)
+// land in the readout slot
+template <typename T> nlse_status readout_impl(nlse_grid* g, VT<T>* field_out, T* flu_out) {
+    const KernelSet<T>* ks = Sel<T>::ks(g);
+    double* partials = dat(g, g->lay.partials);
+    cudaError_t e = ks->readout(at<T>(g, g->lay.state), tab<T>(g, g->lay.tw), field_out, flu_out,
+                                partials, g->stream);
+    if (e != cudaSuccess) return NLSE_ECUDA;
+    const double dx = g->p.L / g->p.n;
+    k_finalize<<<1, 256, 0, g->stream>>>(partials, ks->row_blocks, dx * dx, dat(g, g->lay.readout),
+                                         reinterpret_cast<int*>(g->ws + g->lay.status));
+    return cuerr(cudaGetLastError());
+}
+
+nlse_status readout_any(nlse_grid* g, void* field_out, void* flu_out) {
+    if (g->p.precision == NLSE_FP64)
+        return readout_impl<double>(g, (double2*)field_out, (double*)flu_out);
+    return readout_impl<float>(g, (float2*)field_out, (float*)flu_out);
+}
+
+nlse_status fetch_readout(nlse_grid* g, double out[2]) {
+    cudaError_t e = cudaMemcpyAsync(out, g->ws + g->lay.readout, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, g->stream);
+    if (e != cudaSuccess) return NLSE_ECUDA;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return NLSE_ECUDA;
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1])) return NLSE_ENONFINITE;
+    return NLSE_OK;
+}
+
+template <typename T> nlse_status upload_tables(nlse_grid* g) {
+    std::vector<double> px, py, tw;
+    propagator_tables(&g->p, px, py);
+    twiddle_table(g->p.n, tw);
+    std::vector<T> a, b, c;
+    round_table(px, a);
+    round_table(py, b);
+    round_table(tw, c);
+    const size_t bytes = a.size() * sizeof(T);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(g->ws + g->lay.px, a.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
+        return NLSE_ECUDA;
+    if ((e = cudaMemcpyAsync(g->ws + g->lay.py, b.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
+        return NLSE_ECUDA;
+    if ((e = cudaMemcpyAsync(g->ws + g->lay.tw, c.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
+        return NLSE_ECUDA;
+    // the host vectors die at return: make the copies complete first
+    return cuerr(cudaStreamSynchronize(g->stream));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+
+extern "C" {
+
+const char* nlse_status_string(nlse_status s) {
+    switch (s) {
+        case NLSE_OK: return "NLSE_OK";
+        case NLSE_EINVAL: return "NLSE_EINVAL: invalid argument";
+        case NLSE_EUNSUPPORTED: return "NLSE_EUNSUPPORTED: unsupported size or precision";
+        case NLSE_ENOMEM: return "NLSE_ENOMEM: workspace too small";
+        case NLSE_ECUDA: return "NLSE_ECUDA: CUDA error";
+        case NLSE_ENONFINITE: return "NLSE_ENONFINITE: non-finite value in the field";
+        case NLSE_ETIMEOUT: return "NLSE_ETIMEOUT: device-side wait timed out";
+        case NLSE_ESTATE: return "NLSE_ESTATE: call out of order";
+    }
+    return "NLSE: unknown status";
+}
+
+int32_t nlse_version(void) { return 10000; }
+
+nlse_status nlse_workspace_size(const nlse_params* p, size_t* bytes) {
+    if (!bytes) return NLSE_EINVAL;
+    nlse_status st = validate(p);
+    if (st != NLSE_OK) return st;
+    *bytes = layout_for(p->n, p->precision).total;
+    return NLSE_OK;
+}
+
+nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_workspace,
+                        size_t workspace_bytes, nlse_grid** out) {
+    if (!out || !dev_workspace) return NLSE_EINVAL;
+    *out = nullptr;
+    nlse_status st = validate(p);
+    if (st != NLSE_OK) return st;
+    if (reinterpret_cast<uintptr_t>(dev_workspace) & 255) return NLSE_EINVAL;
+    Layout lay = layout_for(p->n, p->precision);
+    if (workspace_bytes < lay.total) return NLSE_ENOMEM;
+    nlse_grid* g = new (std::nothrow) nlse_grid();
+    if (!g) return NLSE_ENOMEM;
+    g->p = *p;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    g->ws = static_cast<unsigned char*>(dev_workspace);
+    g->lay = lay;
+    const int k = log2_exact(p->n);
+    if (cudaGetDevice(&g->device) != cudaSuccess) { delete g; return NLSE_ECUDA; }
+    if (p->precision == NLSE_FP64) {
+        g->k64 = kernels_f64(k);
+        g->cols = g->k64->col_default;
+        g->sc64 = screen_coef<double>(p);
+    } else {
+        g->k32 = kernels_f32(k);
+        g->cols = g->k32->col_default;
+        g->sc32 = screen_coef<float>(p);
+    }
+    if (const char* env = std::getenv("NLSE_COL_TILE")) {
+        const int c = std::atoi(env);
+        const int mask = p->precision == NLSE_FP64 ? g->k64->col_mask : g->k32->col_mask;
+        for (int i = 0; i < 5; ++i)
+            if (kColOptions[i] == c && ((mask >> i) & 1)) g->cols = c;
+    }
+    st = p->precision == NLSE_FP64 ? upload_tables<double>(g) : upload_tables<float>(g);
+    if (st == NLSE_OK)
+        st = cuerr(cudaMemsetAsync(g->ws + lay.status, 0, sizeof(int), g->stream));
+    if (st != NLSE_OK) { delete g; return st; }
+    *out = g;
+    return NLSE_OK;
+}
+
+nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device) {
+    if (!g || !src) return NLSE_EINVAL;
+    const size_t cs = g->p.precision == NLSE_FP64 ? 16 : 8;
+    const size_t bytes = (size_t)g->p.n * g->p.n * cs;
+    void* state = g->ws + g->lay.state;
+    cudaError_t e;
+    if (src_on_device) {
+        // forward row transform straight from the caller's buffer
+        if (g->p.precision == NLSE_FP64)
+            e = g->k64->row_forward((const double2*)src, (double2*)state, tab<double>(g, g->lay.tw), g->stream);
+        else
+            e = g->k32->row_forward((const float2*)src, (float2*)state, tab<float>(g, g->lay.tw), g->stream);
+    } else {
+        e = cudaMemcpyAsync(state, src, bytes, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) {
+            if (g->p.precision == NLSE_FP64)
+                e = g->k64->row_forward((const double2*)state, (double2*)state, tab<double>(g, g->lay.tw), g->stream);
+            else
+                e = g->k32->row_forward((const float2*)state, (float2*)state, tab<float>(g, g->lay.tw), g->stream);
+        }
+    }
+    if (e != cudaSuccess) return NLSE_ECUDA;
+    g->steps = 0;
+    g->hist_count = 0;
+    g->loaded = 1;
+    return NLSE_OK;
+}
+
+nlse_status nlse_step(nlse_grid* g, int32_t nsteps) {
+    if (!g || nsteps < 0) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    return g->p.precision == NLSE_FP64 ? step_impl<double>(g, nsteps) : step_impl<float>(g, nsteps);
+}
+
+nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double* row_ms) {
+    if (!g || nsteps < 0) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    std::vector<cudaEvent_t> ev(2 * (size_t)nsteps + 1, nullptr);
+    nlse_status st = NLSE_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; st = NLSE_ECUDA; break; }
+    if (st == NLSE_OK)
+        st = g->p.precision == NLSE_FP64 ? step_impl<double>(g, nsteps, ev.data())
+                                         : step_impl<float>(g, nsteps, ev.data());
+    double c = 0.0, r = 0.0;
+    if (st == NLSE_OK && nsteps > 0) {
+        if (cudaEventSynchronize(ev[2 * (size_t)nsteps]) != cudaSuccess) st = NLSE_ECUDA;
+        for (int s = 0; st == NLSE_OK && s < nsteps; ++s) {
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, ev[2 * s], ev[2 * s + 1]) != cudaSuccess ||
+                cudaEventElapsedTime(&b, ev[2 * s + 1], ev[2 * s + 2]) != cudaSuccess)
+                st = NLSE_ECUDA;
+            c += a;
+            r += b;
+        }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (st == NLSE_OK) {
+        if (col_ms) *col_ms += c;
+        if (row_ms) *row_ms += r;
+    }
+    return st;
+}
+
+nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps) {
+    if (!g || !steps) return NLSE_EINVAL;
+    *steps = g->steps;
+    return NLSE_OK;
+}
+
+nlse_status nlse_power(nlse_grid* g, double* watts) {
+    if (!g || !watts) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    nlse_status st = readout_any(g, nullptr, nullptr);
+    if (st != NLSE_OK) return st;
+    double r[2];
+    st = fetch_readout(g, r);
+    *watts = r[0];
+    return st;
+}
+
+nlse_status nlse_peak(nlse_grid* g, double* w_per_cm2) {
+    if (!g || !w_per_cm2) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    nlse_status st = readout_any(g, nullptr, nullptr);
+    if (st != NLSE_OK) return st;
+    double r[2];
+    st = fetch_readout(g, r);
+    *w_per_cm2 = r[1];
+    return st;
+}
+
+nlse_status nlse_fluence(nlse_grid* g, void* dst, int dst_on_device, int downsample) {
+    if (!g || !dst) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    const int n = g->p.n;
+    if (downsample < 1 || (downsample & (downsample - 1)) || downsample > n) return NLSE_EINVAL;
+    const bool f64 = g->p.precision == NLSE_FP64;
+    const size_t rs = f64 ? 8 : 4;
+    unsigned char* flu = g->ws + g->lay.aux;          // n^2 reals
+    unsigned char* box = flu + (size_t)n * n * rs;    // (n/ds)^2 reals (second half of aux)
+    const bool direct = dst_on_device && downsample == 1;
+    nlse_status st = readout_any(g, nullptr, direct ? dst : flu);
+    if (st != NLSE_OK) return st;
+    const int m = n / downsample;
+    const size_t out_bytes = (size_t)m * m * rs;
+    if (downsample > 1) {
+        void* target = dst_on_device ? dst : box;
+        const int blocks = (int)(((size_t)m * m + 255) / 256) < 4096 ? (int)(((size_t)m * m + 255) / 256) : 4096;
+        if (f64) k_box_mean<double><<<blocks, 256, 0, g->stream>>>((const double*)flu, (double*)target, n, downsample);
+        else k_box_mean<float><<<blocks, 256, 0, g->stream>>>((const float*)flu, (float*)target, n, downsample);
+        if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+        if (!dst_on_device) {
+            if (cudaMemcpyAsync(dst, box, out_bytes, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+                return NLSE_ECUDA;
+            return cuerr(cudaStreamSynchronize(g->stream));
+        }
+        return NLSE_OK;
+    }
+    if (!dst_on_device) {
+        if (cudaMemcpyAsync(dst, flu, out_bytes, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        return cuerr(cudaStreamSynchronize(g->stream));
+    }
+    return NLSE_OK;
+}
+
+nlse_status nlse_read_field(nlse_grid* g, void* dst, int dst_on_device) {
+    if (!g || !dst) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    const size_t cs = g->p.precision == NLSE_FP64 ? 16 : 8;
+    const size_t bytes = (size_t)g->p.n * g->p.n * cs;
+    void* target = dst_on_device ? dst : (void*)(g->ws + g->lay.aux);
+    nlse_status st = readout_any(g, target, nullptr);
+    if (st != NLSE_OK) return st;
+    if (!dst_on_device) {
+        if (cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        return cuerr(cudaStreamSynchronize(g->stream));
+    }
+    return NLSE_OK;
+}
+
+nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capacity, int32_t* count) {
+    if (!g || !count || capacity < 0) return NLSE_EINVAL;
+    const int64_t have = g->hist_count < kHistCap ? g->hist_count : kHistCap;
+    const int64_t first = g->hist_count - have;
+    std::vector<double> buf(2 * (size_t)kHistCap);
+    if (have > 0) {
+        if (cudaMemcpyAsync(buf.data(), g->ws + g->lay.hist, buf.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        if (cudaStreamSynchronize(g->stream) != cudaSuccess) return NLSE_ECUDA;
+    }
+    const int64_t ncopy = have < capacity ? have : capacity;
+    for (int64_t i = 0; i < ncopy; ++i) {
+        const int64_t slot = (first + i) % kHistCap;
+        if (power) power[i] = buf[2 * slot];
+        if (peak) peak[i] = buf[2 * slot + 1];
+    }
+    *count = (int32_t)ncopy;
+    return NLSE_OK;
+}
+
+nlse_status nlse_device_status(nlse_grid* g) {
+    if (!g) return NLSE_EINVAL;
+    int word = 0;
+    if (cudaMemcpyAsync(&word, g->ws + g->lay.status, sizeof(int), cudaMemcpyDeviceToHost, g->stream) !=
+        cudaSuccess)
+        return NLSE_ECUDA;
+    if (cudaMemsetAsync(g->ws + g->lay.status, 0, sizeof(int), g->stream) != cudaSuccess) return NLSE_ECUDA;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return NLSE_ECUDA;
+    if (word & 2) return NLSE_ETIMEOUT;
+    if (word & 1) return NLSE_ENONFINITE;
+    return NLSE_OK;
+}
+
+nlse_status nlse_destroy(nlse_grid* g) {
+    if (!g) return NLSE_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    delete g;
+    return cuerr(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// dispatch.cuh -- host-side launchers of the march kernels for every supported
+// grid size n = 2^k (8..8192) and precision, gathered into per-size tables.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace nlse {
+
+constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per block (sm_100/103)
+constexpr int kColOptions[5] = {1, 2, 4, 8, 16};
+
+template <typename T> struct KernelSet {
+    using V = typename vec2<T>::type;
+    using W = typename tab_of<T>::type;
+    int n;
+    int row_blocks;    // blocks of the row-oriented kernels (n / rows_per_block)
+    int col_mask;      // bit i set: column tile kColOptions[i] is instantiated
+    int col_default;   // default column tile
+    cudaError_t (*row_pass)(V* field, const W* tw, ScreenCoef<T> sc, double* partials, bool diag,
+                            cudaStream_t s);
+    cudaError_t (*col_pass)(V* field, const W* tw, const W* px, const W* py, int cols,
+                            cudaStream_t s);
+    cudaError_t (*row_forward)(const V* src, V* dst, const W* tw, cudaStream_t s);
+    cudaError_t (*readout)(const V* state, const W* tw, V* field_out, T* flu_out, double* partials,
+                           cudaStream_t s);
+};
+
+// Raise the dynamic shared-memory limit of one kernel once per device.  The
+// record is per kernel (the template argument is the kernel itself).
+template <auto Kernel> inline cudaError_t ensure_smem(int bytes) {
+    static unsigned long long done = 0;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+
+template <typename T, int N> constexpr int row_smem_bytes() {
+    return line_stride<T, N, rows_per_block<T, N>()>() * rows_per_block<T, N>() *
+           (int)sizeof(typename vec2<T>::type);
+}
+template <typename T, int N, int C> constexpr int col_smem_bytes() {
+    return line_stride<T, N, C>() * C * (int)sizeof(typename vec2<T>::type);
+}
+template <typename T, int N, int C> constexpr bool col_valid() {
+    return C <= N && threads_per_line<T, N>() * C <= 1024 && col_smem_bytes<T, N, C>() <= kMaxSmem;
+}
+
+template <typename T, int N>
+cudaError_t launch_row_pass(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
+                            ScreenCoef<T> sc, double* partials, bool diag, cudaStream_t s) {
+    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
+    constexpr int SMEM = row_smem_bytes<T, N>();
+    cudaError_t e;
+    if (diag) {
+        if ((e = ensure_smem<k_row_pass<T, N, true>>(SMEM)) != cudaSuccess) return e;
+        k_row_pass<T, N, true><<<N / RPB, THREADS, SMEM, s>>>(field, tw, sc, partials);
+    } else {
+        if ((e = ensure_smem<k_row_pass<T, N, false>>(SMEM)) != cudaSuccess) return e;
+        k_row_pass<T, N, false><<<N / RPB, THREADS, SMEM, s>>>(field, tw, sc, partials);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int N, int C>
+cudaError_t launch_col_c(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
+                         const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
+                         cudaStream_t s) {
+    if constexpr (col_valid<T, N, C>()) {
+        constexpr int SMEM = col_smem_bytes<T, N, C>();
+        cudaError_t e = ensure_smem<k_col_pass<T, N, C>>(SMEM);
+        if (e != cudaSuccess) return e;
+        k_col_pass<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(field, tw, px, py);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidConfiguration;
+    }
+}
+
+template <typename T, int N>
+cudaError_t launch_col_pass(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
+                            const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
+                            int cols, cudaStream_t s) {
+    switch (cols) {
+        case 1: return launch_col_c<T, N, 1>(field, tw, px, py, s);
+        case 2: return launch_col_c<T, N, 2>(field, tw, px, py, s);
+        case 4: return launch_col_c<T, N, 4>(field, tw, px, py, s);
+        case 8: return launch_col_c<T, N, 8>(field, tw, px, py, s);
+        case 16: return launch_col_c<T, N, 16>(field, tw, px, py, s);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+template <typename T, int N>
+cudaError_t launch_row_forward(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                               const typename tab_of<T>::type* tw, cudaStream_t s) {
+    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
+    constexpr int SMEM = row_smem_bytes<T, N>();
+    cudaError_t e = ensure_smem<k_row_forward<T, N>>(SMEM);
+    if (e != cudaSuccess) return e;
+    k_row_forward<T, N><<<N / RPB, THREADS, SMEM, s>>>(src, dst, tw);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_readout(const typename vec2<T>::type* state, const typename tab_of<T>::type* tw,
+                           typename vec2<T>::type* field_out, T* flu_out, double* partials,
+                           cudaStream_t s) {
+    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
+    constexpr int SMEM = row_smem_bytes<T, N>();
+    cudaError_t e = ensure_smem<k_readout<T, N>>(SMEM);
+    if (e != cudaSuccess) return e;
+    k_readout<T, N><<<N / RPB, THREADS, SMEM, s>>>(state, tw, field_out, flu_out, partials);
+    return cudaGetLastError();
+}
+
+template <typename T, int N> constexpr int col_mask() {
+    return (col_valid<T, N, 1>() ? 1 : 0) | (col_valid<T, N, 2>() ? 2 : 0) |
+           (col_valid<T, N, 4>() ? 4 : 0) | (col_valid<T, N, 8>() ? 8 : 0) |
+           (col_valid<T, N, 16>() ? 16 : 0);
+}
+
+// default column tile: the widest tile whose block stays within 512 threads and
+// ~113 KB of shared memory (two resident blocks per SM), else the widest valid
+template <typename T, int N> constexpr int col_default() {
+    int best = 0;
+    for (int i = 0; i < 5; ++i) {
+        const int c = kColOptions[i];
+        const bool valid = (col_mask<T, N>() >> i) & 1;
+        const int thr = threads_per_line<T, N>() * c;
+        const int sm = line_stride<T, N, 1>() * c * (int)sizeof(typename vec2<T>::type);
+        if (valid && thr <= 512 && sm <= kMaxSmem / 2) best = c;
+    }
+    if (best == 0)
+        for (int i = 0; i < 5; ++i)
+            if ((col_mask<T, N>() >> i) & 1) best = kColOptions[i];
+    return best;
+}
+
+template <typename T, int N> KernelSet<T> make_set() {
+    KernelSet<T> k;
+    k.n = N;
+    k.row_blocks = N / rows_per_block<T, N>();
+    k.col_mask = col_mask<T, N>();
+    k.col_default = col_default<T, N>();
+    k.row_pass = &launch_row_pass<T, N>;
+    k.col_pass = &launch_col_pass<T, N>;
+    k.row_forward = &launch_row_forward<T, N>;
+    k.readout = &launch_readout<T, N>;
+    return k;
+}
+
+// defined in nlse_f32.cu / nlse_f64.cu: table for n = 2^log2n, or nullptr
+const KernelSet<float>* kernels_f32(int log2n);
+const KernelSet<double>* kernels_f64(int log2n);
+
+}  // namespace nlse

@@ -1,0 +1,250 @@
+// fft.cuh -- register/shared-memory FFT engine for one-dimensional complex
+// transforms of length N = 2^n, used by the row and column passes of the
+// split-step march (arXiv 2306.15678, Eq. 2: the diffraction operator is
+// applied in Fourier space).
+//
+// Data layout.  A group of T = N/E threads holds one transform; thread j holds
+// E elements in registers, element m being x[j + m*T].  This layout is both the
+// input layout (coalesced global loads: consecutive threads read consecutive
+// addresses) and the output layout (natural frequency order, coalesced stores).
+//
+// Algorithm.  Stockham autosort, radix R <= E per pass (R = E except for a
+// smaller final radix): for butterfly b (0 <= b < N/R) with stride NS (product
+// of the earlier radices) and k = b mod NS,
+//     a_r = x[b + r N/R] * W_{NS R}^{r k},   (a_0..a_{R-1}) <- DFT_R(a),
+//     y[(b / NS) NS R + k + r NS] = a_r.
+// The inputs of a thread's butterflies are exactly its registers; only the
+// outputs of non-final passes go through shared memory (one padded exchange per
+// pass boundary), and the final pass writes each result back into the register
+// it came from, in natural order.  Forward is e^{-2 pi i nk/N}, unnormalised;
+// the inverse uses conjugate twiddles, also unnormalised.
+//
+// Twiddles W_N^i = exp(-2 pi i i/N), i < N, come from a table built in FP64 on
+// the host.  In FP32 every twiddle, radix constant and propagator factor is
+// held as an unevaluated pair hi + lo (hi = fl32(w), lo = fl32(w - hi)) and
+// multiplied with FMA chains, so that the factor is exact to O(eps^2): the
+// same factors are applied at every z step, and a rounded factor would act as
+// a fixed operator error that accumulates linearly over thousands of steps.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nlse {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+
+template <typename V> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+template <typename V> __device__ __forceinline__ V mk(typename real_of<V>::type x,
+                                                      typename real_of<V>::type y) {
+    V r; r.x = x; r.y = y; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+    return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, typename real_of<V>::type s) {
+    return mk<V>(a.x * s, a.y * s);
+}
+
+// table entry of twiddles and propagator factors: (hi.re, hi.im, lo.re, lo.im)
+// in FP32, the value itself in FP64
+template <typename T> struct tab_of;
+template <> struct tab_of<float> { using type = float4; };
+template <> struct tab_of<double> { using type = double2; };
+
+// a * w (CONJ = false) or a * conj(w) (CONJ = true), w an exact-to-eps^2 table entry
+template <bool CONJ> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
+    float2 r;
+    if constexpr (!CONJ) {
+        r.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, fmaf(a.x, w.z, -a.y * w.w)));
+        r.y = fmaf(a.x, w.y, fmaf(a.y, w.x, fmaf(a.x, w.w, a.y * w.z)));
+    } else {
+        r.x = fmaf(a.x, w.x, fmaf(a.y, w.y, fmaf(a.x, w.z, a.y * w.w)));
+        r.y = fmaf(a.y, w.x, fmaf(-a.x, w.y, fmaf(a.y, w.z, -a.x * w.w)));
+    }
+    return r;
+}
+template <bool CONJ> __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
+    return CONJ ? cmulc(a, w) : cmul(a, w);
+}
+
+// multiply by W_4^1: -i in the forward transform, +i in the inverse
+template <bool INV, typename V> __device__ __forceinline__ V rot4(V a) {
+    return INV ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
+
+// x*c with c given in double: one rounding in FP64, hi/lo pair in FP32
+__device__ __forceinline__ float mulc(float x, double c) {
+    const float h = (float)c, l = (float)(c - (double)h);
+    return fmaf(x, h, x * l);
+}
+__device__ __forceinline__ double mulc(double x, double c) { return x * c; }
+// x*c + y*d with constants c, d
+__device__ __forceinline__ float dotc(float x, double c, float y, double d) {
+    const float ch = (float)c, cl = (float)(c - (double)ch);
+    const float dh = (float)d, dl = (float)(d - (double)dh);
+    return fmaf(x, ch, fmaf(y, dh, fmaf(x, cl, y * dl)));
+}
+__device__ __forceinline__ double dotc(double x, double c, double y, double d) { return x * c + y * d; }
+
+// multiply by the constant W_16^J (forward) or its conjugate (inverse)
+template <int J, bool INV, typename V> __device__ __forceinline__ V w16(V a) {
+    constexpr int j = J & 15;
+    constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173,
+                     r2 = 0.70710678118654752440;
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 4) {
+        return rot4<INV>(a);
+    } else if constexpr (j == 8) {
+        return mk<V>(-a.x, -a.y);
+    } else if constexpr (j == 12) {
+        return rot4<!INV>(a);
+    } else if constexpr ((j & 1) == 0) {
+        // W_16^j = r2 (cx - i sx) with cx, sx = +-1 (j = 2, 6, 10, 14)
+        constexpr int cx = (j == 2 || j == 14) ? 1 : -1;
+        constexpr int sx = (j == 2 || j == 6) ? 1 : -1;
+        // forward: (x + i y)(cx - i sx) = (cx x + sx y) + i (cx y - sx x); inverse: sx -> -sx
+        constexpr int ss = INV ? -sx : sx;
+        const auto re = cx * a.x + ss * a.y;
+        const auto im = cx * a.y - ss * a.x;
+        return mk<V>(mulc(re, r2), mulc(im, r2));
+    } else {
+        // W_16^j = cos(2 pi j/16) - i sin(2 pi j/16)
+        constexpr double c = j == 1 ? c1 : j == 3 ? s1 : j == 5 ? -s1 : j == 7 ? -c1
+                           : j == 9 ? -c1 : j == 11 ? -s1 : j == 13 ? s1 : c1;
+        constexpr double sn = j == 1 ? s1 : j == 3 ? c1 : j == 5 ? c1 : j == 7 ? s1
+                            : j == 9 ? -s1 : j == 11 ? -c1 : j == 13 ? -c1 : -s1;
+        // forward: (x + i y)(c - i s); inverse: (x + i y)(c + i s)
+        if constexpr (INV) return mk<V>(dotc(a.x, c, a.y, -sn), dotc(a.x, sn, a.y, c));
+        else return mk<V>(dotc(a.x, c, a.y, sn), dotc(a.y, c, a.x, -sn));
+    }
+}
+
+// ----------------------------------------------------------------- DFT_R --
+
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a0, V& a1) {
+    V t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
+    V t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    V t2 = cadd(a1, a3), t3 = rot4<INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V (&a)[R]) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        dft2<INV>(a[0], a[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(a[0], a[1], a[2], a[3]);
+    } else if constexpr (R == 8) {
+        // 8 = 2 x 4: even/odd DFT4 then combine with W_8^k = W_16^(2k)
+        dft4<INV>(a[0], a[2], a[4], a[6]);
+        dft4<INV>(a[1], a[3], a[5], a[7]);
+        V o1 = w16<2, INV>(a[3]), o2 = w16<4, INV>(a[5]), o3 = w16<6, INV>(a[7]);
+        V e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+        a[0] = cadd(e0, a[1]); a[4] = csub(e0, a[1]);
+        a[1] = cadd(e1, o1);   a[5] = csub(e1, o1);
+        a[2] = cadd(e2, o2);   a[6] = csub(e2, o2);
+        a[3] = cadd(e3, o3);   a[7] = csub(e3, o3);
+    } else if constexpr (R == 16) {
+        // 16 = 4 x 4: Y[n2][k1] = DFT4_n1 x[4 n1 + n2]; Y *= W_16^(n2 k1);
+        // X[k1 + 4 k2] = DFT4_n2 Y[n2][k1]
+        dft4<INV>(a[0], a[4], a[8], a[12]);
+        dft4<INV>(a[1], a[5], a[9], a[13]);
+        dft4<INV>(a[2], a[6], a[10], a[14]);
+        dft4<INV>(a[3], a[7], a[11], a[15]);
+        // after these, a[n2 + 4 k1] holds Y[n2][k1]
+        a[5] = w16<1, INV>(a[5]);  a[9] = w16<2, INV>(a[9]);  a[13] = w16<3, INV>(a[13]);
+        a[6] = w16<2, INV>(a[6]);  a[10] = w16<4, INV>(a[10]); a[14] = w16<6, INV>(a[14]);
+        a[7] = w16<3, INV>(a[7]);  a[11] = w16<6, INV>(a[11]); a[15] = w16<9, INV>(a[15]);
+        dft4<INV>(a[0], a[1], a[2], a[3]);     // k1 = 0 -> X[0], X[4], X[8], X[12]
+        dft4<INV>(a[4], a[5], a[6], a[7]);     // k1 = 1 -> X[1], X[5], X[9], X[13]
+        dft4<INV>(a[8], a[9], a[10], a[11]);   // k1 = 2
+        dft4<INV>(a[12], a[13], a[14], a[15]); // k1 = 3
+        // now a[4 k1 + k2] = X[k1 + 4 k2]; transpose the 4x4 index
+        V t;
+        t = a[1]; a[1] = a[4]; a[4] = t;
+        t = a[2]; a[2] = a[8]; a[8] = t;
+        t = a[3]; a[3] = a[12]; a[12] = t;
+        t = a[6]; a[6] = a[9]; a[9] = t;
+        t = a[7]; a[7] = a[13]; a[13] = t;
+        t = a[11]; a[11] = a[14]; a[14] = t;
+    } else {
+        static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
+    }
+}
+
+// --------------------------------------------------------- Stockham passes --
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// padded shared-memory index: one spare slot every E elements keeps the
+// strided exchange writes free of bank conflicts
+template <int E> __device__ __forceinline__ int padix(int p) { return p + (p >> ilog2(E)); }
+template <int N, int E> __host__ __device__ constexpr int padded_len() { return N + N / E; }
+
+// Transform held in v (layout above).  `sm` points at this group's padded
+// shared-memory line (padded_len<N,E>() elements); every thread of the block
+// must call this function (it contains __syncthreads()).
+template <typename V, int N, int E, bool INV, int NS = 1>
+__device__ __forceinline__ void fft_stockham(
+    V (&v)[E], V* sm, const typename tab_of<typename real_of<V>::type>::type* __restrict__ tw, int j) {
+    constexpr int REM = N / NS;
+    constexpr int R = REM >= E ? E : REM;
+    constexpr bool LAST = (NS * R == N);
+    constexpr int T = N / E;
+    constexpr int B = E / R;
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const int b = j + i * T;
+        V a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
+        int k = 0;
+        if constexpr (NS > 1) {
+            k = b & (NS - 1);
+            constexpr int STRIDE = N / (NS * R);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                a[r] = twmul<INV>(a[r], __ldg(&tw[(r * k) * STRIDE]));
+            }
+        }
+        dft<R, INV>(a);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i + r * B] = a[r];
+        } else {
+            const int base = ((b >> ilog2(NS)) << ilog2(NS * R)) + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[padix<E>(base + r * NS)] = a[r];
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = sm[padix<E>(j + m * T)];
+        __syncthreads();
+        fft_stockham<V, N, E, INV, NS * R>(v, sm, tw, j);
+    }
+}
+
+}  // namespace nlse

@@ -1,0 +1,135 @@
+"""Python view of one transverse grid marched by the C ABI (include/nlse.h).
+
+PyTorch owns the device workspace and supplies the CUDA stream; libnlse.so does
+all the work.  Host arrays are numpy; device arrays are torch tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+_PREC = {"fp64": capi.NLSE_FP64, "fp32": capi.NLSE_FP32}
+
+
+def make_params(cfg: dict, precision: str | None = None, diag_every: int = 0) -> capi.nlse_params:
+    """nlse_params from a workload dict of ``configs`` (physical units)."""
+    p = capi.nlse_params()
+    p.n = int(cfg["n"])
+    p.K = int(cfg["K"])
+    p.terms = int(cfg["terms"])
+    p.precision = _PREC[precision or cfg.get("precision", "fp32")]
+    for f in ("L", "dz", "lambda0", "n0", "n2", "sigmaK", "rho_nt", "rho_c", "tau_pl", "betaK"):
+        setattr(p, f, float(cfg[f]))
+    th = cfg.get("theta", (1.0, 0.0, 1.0, 0.0, 1.0, 0.0))
+    for i in range(6):
+        p.theta[i] = float(th[i])
+    p.diag_every = int(diag_every)
+    p.reserved = 0
+    return p
+
+
+def _aligned_workspace(nbytes: int, device) -> tuple[torch.Tensor, int]:
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    ptr = buf.data_ptr()
+    return buf, (ptr + 255) & ~255
+
+
+class Grid:
+    """One n x n field marched by split-step Fourier steps on the GPU."""
+
+    def __init__(self, cfg: dict, precision: str | None = None, diag_every: int = 0,
+                 device: str | torch.device | None = None, stream: torch.cuda.Stream | None = None):
+        self.cfg = cfg
+        self.params = make_params(cfg, precision, diag_every)
+        self.n = int(cfg["n"])
+        self.precision = "fp64" if self.params.precision == capi.NLSE_FP64 else "fp32"
+        self.cdtype = np.complex128 if self.precision == "fp64" else np.complex64
+        self.rdtype = np.float64 if self.precision == "fp64" else np.float32
+        self.tcdtype = torch.complex128 if self.precision == "fp64" else torch.complex64
+        self.trdtype = torch.float64 if self.precision == "fp64" else torch.float32
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.ws_bytes = capi.nlse_workspace_size(self.params)
+        self._ws, ptr = _aligned_workspace(self.ws_bytes, self.device)
+        self.h = capi.nlse_create(self.params, self.stream.cuda_stream, ptr, self.ws_bytes)
+        self._keep = None
+
+    # ------------------------------------------------------------------ io
+    def load(self, U) -> "Grid":
+        if isinstance(U, torch.Tensor) and U.is_cuda:
+            t = U.to(self.tcdtype).contiguous()
+            self._keep = t
+            capi.nlse_load_field(self.h, t.data_ptr(), True)
+        else:
+            a = np.ascontiguousarray(U.cpu().numpy() if isinstance(U, torch.Tensor) else U,
+                                     dtype=self.cdtype)
+            assert a.shape == (self.n, self.n)
+            capi.nlse_load_field(self.h, a.ctypes.data, False)
+        return self
+
+    def step(self, nsteps: int = 1) -> "Grid":
+        capi.nlse_step(self.h, int(nsteps))
+        return self
+
+    def step_timed(self, nsteps: int) -> tuple[float, float]:
+        """Step and return summed (column-pass, row-pass) kernel times in ms."""
+        return capi.nlse_step_timed(self.h, int(nsteps))
+
+    @property
+    def steps_taken(self) -> int:
+        return capi.nlse_steps_taken(self.h)
+
+    def power(self) -> float:
+        return capi.nlse_power(self.h)
+
+    def peak(self) -> float:
+        return capi.nlse_peak(self.h)
+
+    def field(self, device: bool = False):
+        if device:
+            out = torch.empty((self.n, self.n), dtype=self.tcdtype, device=self.device)
+            capi.nlse_read_field(self.h, out.data_ptr(), True)
+            return out
+        out = np.empty((self.n, self.n), dtype=self.cdtype)
+        capi.nlse_read_field(self.h, out.ctypes.data, False)
+        return out
+
+    def fluence(self, downsample: int = 1, device: bool = False):
+        m = self.n // downsample
+        if device:
+            out = torch.empty((m, m), dtype=self.trdtype, device=self.device)
+            capi.nlse_fluence(self.h, out.data_ptr(), True, downsample)
+            return out
+        out = np.empty((m, m), dtype=self.rdtype)
+        capi.nlse_fluence(self.h, out.ctypes.data, False, downsample)
+        return out
+
+    def history(self):
+        cap = 4096
+        pw = np.empty(cap)
+        pk = np.empty(cap)
+        c = capi.nlse_history(self.h, pw.ctypes.data, pk.ctypes.data, cap)
+        return pw[:c].copy(), pk[:c].copy()
+
+    def device_status(self) -> int:
+        return capi.nlse_device_status(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            capi.nlse_destroy(self.h)
+            self.h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports every
+function include/nlse.h declares, and validates arguments before any CUDA call."""
+import os
+import re
+
+import pytest
+
+from paper_2306_15678_gb300 import capi, configs
+from paper_2306_15678_gb300.grid import make_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(nlse_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function():
+    lib = capi.lib()
+    decl = declared_functions()
+    assert len(decl) >= 14
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(decl) == set(capi.exported_symbols())
+
+
+def test_status_strings_and_version():
+    for s in range(8):
+        assert capi.nlse_status_string(s).startswith("NLSE")
+    assert capi.nlse_version() >= 10000
+
+
+def test_workspace_size_and_validation_on_host():
+    cfg = configs.cfg_dense_fp32()
+    p = make_params(cfg)
+    ws = capi.nlse_workspace_size(p)
+    assert ws >= 2 * 4096 * 4096 * 8
+    p64 = make_params(cfg, precision="fp64")
+    assert capi.nlse_workspace_size(p64) >= 2 * 4096 * 4096 * 16
+    bad = [("n", 100, capi.NLSE_EINVAL), ("n", 16384, capi.NLSE_EUNSUPPORTED),
+           ("n", 4, capi.NLSE_EUNSUPPORTED), ("precision", 7, capi.NLSE_EUNSUPPORTED),
+           ("K", 0, capi.NLSE_EINVAL), ("terms", 16, capi.NLSE_EINVAL),
+           ("L", -1.0, capi.NLSE_EINVAL), ("dz", 0.0, capi.NLSE_EINVAL),
+           ("diag_every", -1, capi.NLSE_EINVAL), ("reserved", 1, capi.NLSE_EINVAL)]
+    for field, val, code in bad:
+        q = make_params(cfg)
+        setattr(q, field, val)
+        with pytest.raises(capi.NlseError) as ei:
+            capi.nlse_workspace_size(q)
+        assert ei.value.status == code, (field, val)
+
+
+def test_create_rejects_bad_workspace_before_any_launch():
+    p = make_params(configs.cfg_plain_fp64())
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_create(p, 0, 0, 1 << 20)
+    assert ei.value.status == capi.NLSE_EINVAL
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_create(p, 0, 256 * 1024, 1024)  # too small: ENOMEM before touching it
+    assert ei.value.status == capi.NLSE_ENOMEM
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_create(p, 0, 256 * 1024 + 8, 1 << 40)  # misaligned
+    assert ei.value.status == capi.NLSE_EINVAL
