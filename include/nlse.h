@@ -173,6 +173,28 @@ nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capa
  * NLSE_ENONFINITE or NLSE_ETIMEOUT. */
 nlse_status nlse_device_status(nlse_grid* g);
 
+/* Power P = sum |U|^2 dx^2 (dx = L/n) and peak max |U|^2 of a caller's field,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory once
+ * they are running, such as a service that hands all device memory to its own
+ * pool at start-up, or a loop that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause.
+ *   field_dev: device pointer, n x n interleaved complex of `precision`
+ *              (physical field U, row-major), read only;
+ *   n:         1 <= n <= 8192 rows and columns; larger n returns
+ *              NLSE_EUNSUPPORTED before any launch;
+ *   out_dev:   device pointer to 2 doubles, receives (power, peak).
+ * Enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream);
+ * does not synchronise.  The per-row partial sums live in one 128 KiB
+ * __device__ array that every device loading the library keeps until exit and
+ * that every call on a device shares: calls that overlap on the GPU (e.g. on
+ * two streams) race on it, so serialise them.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+nlse_status nlse_power_peak_noalloc(const void* field_dev, int32_t n, int32_t precision, double L,
+                                    void* cuda_stream, double* out_dev);
+
 /* Release the handle (not the caller's workspace).  Synchronises. */
 nlse_status nlse_destroy(nlse_grid* g);
 

@@ -68,6 +68,8 @@ _SIGS = {
     "nlse_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]),
     "nlse_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_power_peak_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "nlse_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
@@ -172,6 +174,15 @@ def nlse_history(h, power_ptr: int, peak_ptr: int, capacity: int) -> int:
 
 def nlse_device_status(h) -> int:
     return int(lib().nlse_device_status(h))
+
+
+def nlse_power_peak_noalloc(field_dev: int, n: int, precision: int, L: float, stream: int,
+                            out_dev: int) -> None:
+    """Enqueue (power, peak) of a device field into out_dev (2 doubles); the
+    library allocates nothing for it (its scratch is a static device array)."""
+    check(lib().nlse_power_peak_noalloc(ctypes.c_void_p(field_dev), int(n), int(precision),
+                                        float(L), ctypes.c_void_p(stream), ctypes.c_void_p(out_dev)),
+          "nlse_power_peak_noalloc")
 
 
 def nlse_destroy(h) -> None:
