@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -100,21 +101,31 @@ void propagator_tables(const nlse_params* p, std::vector<double>& px, std::vecto
     }
 }
 
-// Twiddles W_n^i = exp(-2 pi i i / n), i < n, in FP64.
-void twiddle_table(int n, std::vector<double>& tw) {
-    tw.resize(2 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-        // exact octant symmetry keeps |W| and the table's symmetries exact after rounding
-        const double a = kTwoPi * (double)i / (double)n;
-        tw[2 * i] = std::cos(a);
-        tw[2 * i + 1] = -std::sin(a);
-    }
-    // exact values on the axes
-    for (int i = 0; i < n; i += (n >= 4 ? n / 4 : n)) {
-        const int q = (int)((4LL * i) / n);
-        const double cq[4] = {1.0, 0.0, -1.0, 0.0}, sq[4] = {0.0, -1.0, 0.0, 1.0};
-        tw[2 * i] = cq[q & 3];
-        tw[2 * i + 1] = sq[q & 3];
+// Pass-major twiddle table in FP64 for transforms of length n done with e
+// elements per thread (radix e, last pass possibly smaller): the pass with
+// stride ns and radix r owns (r-1) ns entries, entry (rr-1) ns + k holding
+// W_{ns r}^{rr k} = exp(-2 pi i rr k / (ns r)).  Angles are reduced exactly in
+// integers before the FP64 cos/sin.
+void twiddle_table(int n, int e, std::vector<double>& tw) {
+    tw.assign(2 * (size_t)n, 0.0);
+    int cur = 1, off = 0;
+    while (cur < n) {
+        const int rem = n / cur;
+        const int r = rem >= e ? e : rem;
+        if (cur > 1) {
+            const long long period = (long long)cur * r;
+            for (int rr = 1; rr < r; ++rr)
+                for (int k = 0; k < cur; ++k) {
+                    const long long m = ((long long)rr * k) % period;
+                    const double a = kTwoPi * (double)m / (double)period;
+                    const size_t i = (size_t)off + (size_t)(rr - 1) * cur + k;
+                    const double c = std::cos(a), sn = std::sin(a);
+                    tw[2 * i] = c;
+                    tw[2 * i + 1] = -sn;
+                }
+            off += (r - 1) * cur;
+        }
+        cur *= r;
     }
 }
 
@@ -148,6 +159,7 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     c.im_a = (T)(th[5] * aA);
     c.K = p->K;
     c.active = (p->terms & (NLSE_KERR | NLSE_PLASMA | NLSE_MPA)) ? 1 : 0;
+    c.has_gain = (c.re_k != (T)0 || c.re_p != (T)0 || c.re_a != (T)0) ? 1 : 0;
     return c;
 }
 
@@ -181,6 +193,7 @@ struct nlse_grid {
     int64_t hist_count;
     int loaded;
     int cols;  // column tile of the column pass
+    double theta;  // accumulated global phase of the stored field, mod 2 pi
     const KernelSet<float>* k32;
     const KernelSet<double>* k64;
     ScreenCoef<float> sc32;
@@ -208,6 +221,32 @@ template <typename T> const WT<T>* tab(nlse_grid* g, size_t off) {
 }
 
 template <typename T> VT<T>* at(nlse_grid* g, size_t off) { return reinterpret_cast<VT<T>*>(g->ws + off); }
+
+// Global phase dither.  Eq. 1-3 are invariant under U -> U exp(i a), so each
+// step may turn the whole field by a phase theta_s without changing the
+// physics.  With theta_s = 2 pi frac(s (sqrt5 - 1)/2) (golden-ratio sequence)
+// the spectral values, whose low-k part otherwise rotates by the same small
+// angle every step, land at unrelated positions of the FP32 grid each step, so
+// their rounding errors do not add up coherently.  The accumulated phase is
+// kept here in FP64 and removed whenever the field is read out.
+double step_phase(int64_t step) {
+    return kTwoPi * std::fmod((double)step * 0.61803398874989484820, 1.0);
+}
+template <typename T> WT<T> rot_entry(double theta);
+template <> WT<float> rot_entry<float>(double theta) {
+    const double c = std::cos(theta), s = std::sin(theta);
+    const float ch = (float)c, sh = (float)s;
+    return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+}
+template <> WT<double> rot_entry<double>(double theta) {
+    return make_double2(std::cos(theta), std::sin(theta));
+}
+template <typename T> VT<T> unrot_value(double theta) {
+    VT<T> v;
+    v.x = (T)std::cos(theta);
+    v.y = (T)(-std::sin(theta));
+    return v;
+}
 inline double* dat(nlse_grid* g, size_t off) { return reinterpret_cast<double*>(g->ws + off); }
 
 template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_t* ev = nullptr) {
@@ -220,7 +259,9 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
     const double dx = g->p.L / g->p.n;
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
-        cudaError_t e = ks->col_pass(field, tw, px, py, g->cols, g->stream);
+        const double th = step_phase(g->steps + 1);
+        cudaError_t e = ks->col_pass(field, tw, px, py, rot_entry<T>(th), g->cols, g->stream);
+        g->theta = std::fmod(g->theta + th, kTwoPi);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 1], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const bool diag = g->p.diag_every > 0 && ((g->steps + 1) % g->p.diag_every) == 0;
@@ -245,7 +286,7 @@ template <typename T> nlse_status readout_impl(nlse_grid* g, VT<T>* field_out, T
     const KernelSet<T>* ks = Sel<T>::ks(g);
     double* partials = dat(g, g->lay.partials);
     cudaError_t e = ks->readout(at<T>(g, g->lay.state), tab<T>(g, g->lay.tw), field_out, flu_out,
-                                partials, g->stream);
+                                partials, unrot_value<T>(g->theta), g->stream);
     if (e != cudaSuccess) return NLSE_ECUDA;
     const double dx = g->p.L / g->p.n;
     k_finalize<<<1, 256, 0, g->stream>>>(partials, ks->row_blocks, dx * dx, dat(g, g->lay.readout),
@@ -271,18 +312,21 @@ nlse_status fetch_readout(nlse_grid* g, double out[2]) {
 template <typename T> nlse_status upload_tables(nlse_grid* g) {
     std::vector<double> px, py, tw;
     propagator_tables(&g->p, px, py);
-    twiddle_table(g->p.n, tw);
+    // elements per thread of the kernels: 16 in FP32, 8 in FP64 (at most n)
+    const int ept = std::min(g->p.n, sizeof(T) == 4 ? 16 : 8);
+    twiddle_table(g->p.n, ept, tw);
     std::vector<T> a, b, c;
     round_table(px, a);
     round_table(py, b);
     round_table(tw, c);
     const size_t bytes = a.size() * sizeof(T);
+    const size_t tw_bytes = c.size() * sizeof(T);
     cudaError_t e;
     if ((e = cudaMemcpyAsync(g->ws + g->lay.px, a.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
         return NLSE_ECUDA;
     if ((e = cudaMemcpyAsync(g->ws + g->lay.py, b.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
         return NLSE_ECUDA;
-    if ((e = cudaMemcpyAsync(g->ws + g->lay.tw, c.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
+    if ((e = cudaMemcpyAsync(g->ws + g->lay.tw, c.data(), tw_bytes, cudaMemcpyHostToDevice, g->stream)))
         return NLSE_ECUDA;
     // the host vectors die at return: make the copies complete first
     return cuerr(cudaStreamSynchronize(g->stream));
@@ -382,6 +426,7 @@ nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device) {
     if (e != cudaSuccess) return NLSE_ECUDA;
     g->steps = 0;
     g->hist_count = 0;
+    g->theta = 0.0;
     g->loaded = 1;
     return NLSE_OK;
 }

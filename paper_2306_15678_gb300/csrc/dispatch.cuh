@@ -19,11 +19,11 @@ template <typename T> struct KernelSet {
     int col_default;   // default column tile
     cudaError_t (*row_pass)(V* field, const W* tw, ScreenCoef<T> sc, double* partials, bool diag,
                             cudaStream_t s);
-    cudaError_t (*col_pass)(V* field, const W* tw, const W* px, const W* py, int cols,
+    cudaError_t (*col_pass)(V* field, const W* tw, const W* px, const W* py, W rot, int cols,
                             cudaStream_t s);
     cudaError_t (*row_forward)(const V* src, V* dst, const W* tw, cudaStream_t s);
     cudaError_t (*readout)(const V* state, const W* tw, V* field_out, T* flu_out, double* partials,
-                           cudaStream_t s);
+                           V unrot, cudaStream_t s);
 };
 
 // Raise the dynamic shared-memory limit of one kernel once per device.  The
@@ -71,12 +71,12 @@ cudaError_t launch_row_pass(typename vec2<T>::type* field, const typename tab_of
 template <typename T, int N, int C>
 cudaError_t launch_col_c(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
                          const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
-                         cudaStream_t s) {
+                         typename tab_of<T>::type rot, cudaStream_t s) {
     if constexpr (col_valid<T, N, C>()) {
         constexpr int SMEM = col_smem_bytes<T, N, C>();
         cudaError_t e = ensure_smem<k_col_pass<T, N, C>>(SMEM);
         if (e != cudaSuccess) return e;
-        k_col_pass<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(field, tw, px, py);
+        k_col_pass<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(field, tw, px, py, rot);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidConfiguration;
@@ -86,13 +86,13 @@ cudaError_t launch_col_c(typename vec2<T>::type* field, const typename tab_of<T>
 template <typename T, int N>
 cudaError_t launch_col_pass(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
                             const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
-                            int cols, cudaStream_t s) {
+                            typename tab_of<T>::type rot, int cols, cudaStream_t s) {
     switch (cols) {
-        case 1: return launch_col_c<T, N, 1>(field, tw, px, py, s);
-        case 2: return launch_col_c<T, N, 2>(field, tw, px, py, s);
-        case 4: return launch_col_c<T, N, 4>(field, tw, px, py, s);
-        case 8: return launch_col_c<T, N, 8>(field, tw, px, py, s);
-        case 16: return launch_col_c<T, N, 16>(field, tw, px, py, s);
+        case 1: return launch_col_c<T, N, 1>(field, tw, px, py, rot, s);
+        case 2: return launch_col_c<T, N, 2>(field, tw, px, py, rot, s);
+        case 4: return launch_col_c<T, N, 4>(field, tw, px, py, rot, s);
+        case 8: return launch_col_c<T, N, 8>(field, tw, px, py, rot, s);
+        case 16: return launch_col_c<T, N, 16>(field, tw, px, py, rot, s);
         default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -111,12 +111,12 @@ cudaError_t launch_row_forward(const typename vec2<T>::type* src, typename vec2<
 template <typename T, int N>
 cudaError_t launch_readout(const typename vec2<T>::type* state, const typename tab_of<T>::type* tw,
                            typename vec2<T>::type* field_out, T* flu_out, double* partials,
-                           cudaStream_t s) {
+                           typename vec2<T>::type unrot, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
     cudaError_t e = ensure_smem<k_readout<T, N>>(SMEM);
     if (e != cudaSuccess) return e;
-    k_readout<T, N><<<N / RPB, THREADS, SMEM, s>>>(state, tw, field_out, flu_out, partials);
+    k_readout<T, N><<<N / RPB, THREADS, SMEM, s>>>(state, tw, field_out, flu_out, partials, unrot);
     return cudaGetLastError();
 }
 
@@ -126,20 +126,21 @@ template <typename T, int N> constexpr int col_mask() {
            (col_valid<T, N, 16>() ? 16 : 0);
 }
 
-// default column tile: the widest tile whose block stays within 512 threads and
-// ~113 KB of shared memory (two resident blocks per SM), else the widest valid
+// default column tile: the widest valid tile of at most 512 threads, unless
+// its row segments are shorter than one 32-byte sector, in which case the
+// narrowest valid tile that fills a sector (else the widest valid tile)
 template <typename T, int N> constexpr int col_default() {
+    constexpr int cs = 2 * (int)sizeof(T);
     int best = 0;
     for (int i = 0; i < 5; ++i) {
         const int c = kColOptions[i];
-        const bool valid = (col_mask<T, N>() >> i) & 1;
-        const int thr = threads_per_line<T, N>() * c;
-        const int sm = line_stride<T, N, 1>() * c * (int)sizeof(typename vec2<T>::type);
-        if (valid && thr <= 512 && sm <= kMaxSmem / 2) best = c;
+        if (((col_mask<T, N>() >> i) & 1) && threads_per_line<T, N>() * c <= 512) best = c;
     }
-    if (best == 0)
-        for (int i = 0; i < 5; ++i)
-            if ((col_mask<T, N>() >> i) & 1) best = kColOptions[i];
+    if (best * cs >= 32) return best;
+    for (int i = 0; i < 5; ++i)
+        if (((col_mask<T, N>() >> i) & 1) && kColOptions[i] * cs >= 32) return kColOptions[i];
+    for (int i = 0; i < 5; ++i)
+        if ((col_mask<T, N>() >> i) & 1) best = kColOptions[i];
     return best;
 }
 

@@ -19,8 +19,10 @@
 // it came from, in natural order.  Forward is e^{-2 pi i nk/N}, unnormalised;
 // the inverse uses conjugate twiddles, also unnormalised.
 //
-// Twiddles W_N^i = exp(-2 pi i i/N), i < N, come from a table built in FP64 on
-// the host.  In FP32 every twiddle, radix constant and propagator factor is
+// Twiddles come from a pass-major table built in FP64 on the host: the pass
+// with stride NS and radix R owns (R-1) NS consecutive entries, entry
+// (r-1) NS + k holding W_{NS R}^{r k}.  A warp's loads for one r are then
+// contiguous, and one base address per pass serves all r.  In FP32 every twiddle, radix constant and propagator factor is
 // held as an unevaluated pair hi + lo (hi = fl32(w), lo = fl32(w - hi)) and
 // multiplied with FMA chains, so that the factor is exact to O(eps^2): the
 // same factors are applied at every z step, and a rounded factor would act as
@@ -28,6 +30,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace nlse {
 
@@ -62,6 +66,30 @@ template <typename T> struct tab_of;
 template <> struct tab_of<float> { using type = float4; };
 template <> struct tab_of<double> { using type = double2; };
 
+// Table load through the read-only path at a compile-time byte offset from a
+// per-pass base pointer.  Issued as volatile asm with the offset as an
+// immediate: one base register serves every r of a pass, and the forward and
+// inverse transforms of a kernel cannot share (and keep live) the loaded values.
+template <int OFF> __device__ __forceinline__ float4 ldtab(const float4* base) {
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(base), "n"(OFF * 16));
+    return r;
+}
+template <int OFF> __device__ __forceinline__ double2 ldtab(const double2* base) {
+    double2 r;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2+%3];" : "=d"(r.x), "=d"(r.y) : "l"(base), "n"(OFF * 16));
+    return r;
+}
+
+// compile-time loop helper
+template <int I, int END, typename F> __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < END) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, END>(f);
+    }
+}
+
 // a * w (CONJ = false) or a * conj(w) (CONJ = true), w an exact-to-eps^2 table entry
 template <bool CONJ> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
     float2 r;
@@ -77,6 +105,33 @@ template <bool CONJ> __device__ __forceinline__ float2 twmul(float2 a, float4 w)
 template <bool CONJ> __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
     return CONJ ? cmulc(a, w) : cmul(a, w);
 }
+
+// product of two table entries, as a table entry: in FP32 the hi/lo pairs are
+// multiplied with error-free transformations (exact products by FMA, TwoSum) so
+// that the result is again exact to O(eps^2)
+__device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
+    const float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float4 tabmul(float4 a, float4 b) {
+    // real: ah.x bh.x - ah.y bh.y (+ first-order lo terms)
+    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = -a.y * b.y, e2 = fmaf(-a.y, b.y, -p2);
+    const float sr = p1 + p2, er = two_sum_lo(p1, p2, sr);
+    const float lr = er + e1 + e2 + (a.x * b.z + a.z * b.x - a.y * b.w - a.w * b.y);
+    // imaginary: ah.x bh.y + ah.y bh.x (+ first-order lo terms)
+    const float q1 = a.x * b.y, f1 = fmaf(a.x, b.y, -q1);
+    const float q2 = a.y * b.x, f2 = fmaf(a.y, b.x, -q2);
+    const float si = q1 + q2, ei = two_sum_lo(q1, q2, si);
+    const float li = ei + f1 + f2 + (a.x * b.w + a.z * b.y + a.y * b.z + a.w * b.x);
+    float4 r;
+    r.x = sr + lr;
+    r.z = lr - (r.x - sr);
+    r.y = si + li;
+    r.w = li - (r.y - si);
+    return r;
+}
+__device__ __forceinline__ double2 tabmul(double2 a, double2 b) { return cmul(a, b); }
 
 // multiply by W_4^1: -i in the forward transform, +i in the inverse
 template <bool INV, typename V> __device__ __forceinline__ V rot4(V a) {
@@ -201,6 +256,18 @@ __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x
 template <int E> __device__ __forceinline__ int padix(int p) { return p + (p >> ilog2(E)); }
 template <int N, int E> __host__ __device__ constexpr int padded_len() { return N + N / E; }
 
+// first entry of the twiddle block of the pass with stride ns (see above)
+__host__ __device__ constexpr int twiddle_offset(int n, int e, int ns) {
+    int off = 0, cur = 1;
+    while (cur < ns) {
+        const int rem = n / cur;
+        const int r = rem >= e ? e : rem;
+        if (cur > 1) off += (r - 1) * cur;
+        cur *= r;
+    }
+    return off;
+}
+
 // Transform held in v (layout above).  `sm` points at this group's padded
 // shared-memory line (padded_len<N,E>() elements); every thread of the block
 // must call this function (it contains __syncthreads()).
@@ -222,11 +289,11 @@ __device__ __forceinline__ void fft_stockham(
         int k = 0;
         if constexpr (NS > 1) {
             k = b & (NS - 1);
-            constexpr int STRIDE = N / (NS * R);
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                a[r] = twmul<INV>(a[r], __ldg(&tw[(r * k) * STRIDE]));
-            }
+            const auto* twp = tw + (twiddle_offset(N, E, NS) + k);
+            static_for<1, R>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                a[r] = twmul<INV>(a[r], ldtab<(r - 1) * NS>(twp));
+            });
         }
         dft<R, INV>(a);
         if constexpr (LAST) {

@@ -22,40 +22,111 @@ template <typename T> struct ScreenCoef {
     T inv_iref;
     T re_k, re_p, re_a;
     T im_k, im_p, im_a;
-    int K;       // multiphoton order
-    int active;  // 0: no nonlinear term (screen is the identity)
+    int K;         // multiphoton order
+    int active;    // 0: no nonlinear term (screen is the identity)
+    int has_gain;  // 0: Re s = 0 everywhere (pure phase screen)
 };
 
 template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
     T r = (T)1;
     T b = u;
-    while (e > 0) {  // uniform across the grid: K is a launch constant
-        if (e & 1) r *= b;
+#pragma unroll
+    for (int bit = 0; bit < 5; ++bit) {  // K <= 16; e is uniform across the grid
+        if (e & (1 << bit)) r *= b;
         b *= b;
-        e >>= 1;
     }
     return r;
 }
 
-__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
-__device__ __forceinline__ float exp_(float x) { return expf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
+// sin x and cos x - 1 for the screen phase in FP32: Cody-Waite reduction by
+// pi/2 (two-term constant, FMA) onto [-pi/4, pi/4] and the Taylor polynomials
+// of sin (to x^9) and cos - 1 (to x^10), whose truncation errors there are
+// below 2e-9 and 2e-10.  Returning cos - 1 instead of cos keeps the rounding
+// error of the small screen phases relative to the phase, not to 1.  The
+// reduction stays accurate to |x| ~ 1e5 rad; beyond (a diverged march) the
+// reduced argument is clamped so the results stay bounded.
+__device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
+    const float q = rintf(x * 0.636619772367581343f);   // x / (pi/2)
+    float r = fmaf(-q, 1.57079637050628662f, x);        // pi/2 rounded to FP32
+    r = fmaf(-q, -4.37113900018624283e-8f, r);          // pi/2 - fl32(pi/2)
+    r = fminf(fmaxf(r, -0.7853982f), 0.7853982f);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573192239858906e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(r2, ps, 8.33333333333333333e-3f);
+    ps = fmaf(r2, ps, -1.66666666666666667e-1f);
+    const float sr = fmaf(r * r2, ps, r);                // sin r
+    float pc = fmaf(r2, -2.75573192239858906e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(r2, pc, -1.38888888888888889e-3f);
+    pc = fmaf(r2, pc, 4.16666666666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cr1 = r2 * pc;                           // cos r - 1
+    // x = r + quad pi/2: quad 0 (sr, cr1), 1 (1 + cr1, -sr - 1),
+    // 2 (-sr, -2 - cr1), 3 (-1 - cr1, sr - 1)
+    const int quad = ((int)q) & 3;
+    const bool odd = quad & 1, neg = quad & 2;
+    const float sa = odd ? 1.0f + cr1 : sr;
+    *s = neg ? -sa : sa;
+    *cm1 = odd ? (neg ? sr : -sr) - 1.0f : (neg ? -2.0f - cr1 : cr1);
+}
+
+// exp(x) - 1: Taylor polynomial to x^5 for |x| < 1/16 (error < 3e-11 relative),
+// expf(x) - 1 beyond
+__device__ __forceinline__ float expm1_(float x) {
+    float p = fmaf(x, 8.33333333333333333e-3f, 4.16666666666666667e-2f);
+    p = fmaf(x, p, 1.66666666666666667e-1f);
+    p = fmaf(x, p, 0.5f);
+    const float small = fmaf(x * x, p, x);
+    return fabsf(x) < 0.0625f ? small : expf(x) - 1.0f;
+}
 
 // U = v exp(s(|v|^2)) (Eq. 2: screen evaluated on the field entering it)
-template <typename V, typename T>
-__device__ __forceinline__ V apply_screen(V v, const ScreenCoef<T>& c) {
-    const T I = v.x * v.x + v.y * v.y;
-    const T u = I * c.inv_iref;
-    const T uk1 = ipow(u, c.K - 1);
-    const T uk = uk1 * u;
-    const T re = c.re_k * u + c.re_p * uk + c.re_a * uk1;
-    const T im = c.im_k * u + c.im_p * uk + c.im_a * uk1;
-    const T amp = exp_(re);
-    T sn, cs;
-    sincos_(im, &sn, &cs);
-    const T pr = amp * cs, pi = amp * sn;
-    return mk<V>(v.x * pr - v.y * pi, v.x * pi + v.y * pr);
+template <typename T> __device__ __forceinline__ void screen_exponent(T u, const ScreenCoef<T>& c,
+                                                                      T* re, T* im) {
+    T uk1, uk;
+    if (c.K == 8) {  // the multiphoton order of O2 at 800 nm: u^7 and u^8 by squaring
+        const T u2 = u * u, u4 = u2 * u2;
+        uk1 = u4 * u2 * u;
+        uk = u4 * u4;
+    } else {
+        uk1 = ipow(u, c.K - 1);
+        uk = uk1 * u;
+    }
+    *re = c.re_k * u + c.re_p * uk + c.re_a * uk1;
+    *im = c.im_k * u + c.im_p * uk + c.im_a * uk1;
+}
+
+// FP32: U = v + v d with d = exp(re + i im) - 1 = expm1(re) e^{i im} + (e^{i im} - 1),
+// so that the per-step change, not the field, carries the rounding of the factor
+__device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>& c) {
+    const float u = (v.x * v.x + v.y * v.y) * c.inv_iref;
+    float re, im;
+    screen_exponent(u, c, &re, &im);
+    const float em1 = c.has_gain ? expm1_(re) : 0.0f;  // uniform: pure phase screens skip it
+    float sn, cm1;
+    sin_cosm1(im, &sn, &cm1);
+    const float dre = fmaf(em1, cm1, em1 + cm1);  // (1 + em1)(1 + cm1) - 1
+    const float dim = fmaf(em1, sn, sn);          // (1 + em1) sin
+    // the whole change v d first (accurate relative to itself), then a single
+    // rounding of v + v d: adding the small second-order part after rounding the
+    // first-order part would lose it at every step, coherently
+    const float ddx = fmaf(v.x, dre, -v.y * dim);
+    const float ddy = fmaf(v.x, dim, v.y * dre);
+    float2 r;
+    r.x = v.x + ddx;
+    r.y = v.y + ddy;
+    return r;
+}
+
+// FP64: the factor exp(re) (cos im + i sin im) directly
+__device__ __forceinline__ double2 apply_screen(double2 v, const ScreenCoef<double>& c) {
+    const double u = (v.x * v.x + v.y * v.y) * c.inv_iref;
+    double re, im;
+    screen_exponent(u, c, &re, &im);
+    const double amp = exp(re);
+    double sn, cs;
+    sincos(im, &sn, &cs);
+    const double pr = amp * cs, pi = amp * sn;
+    return mk<double2>(v.x * pr - v.y * pi, v.x * pi + v.y * pr);
 }
 
 // ------------------------------------------------------------- reductions --
@@ -127,6 +198,14 @@ static __global__ void __launch_bounds__(256) k_finalize(const double* __restric
 
 // ----------------------------------------------------------------- passes --
 
+// complex conjugate of every element: the inverse transform is computed as
+// conj(F(conj x)), so each pass emits the forward transform code once and runs
+// it twice (a non-unrolled loop), halving the kernel's instruction footprint
+template <typename V, int E> __device__ __forceinline__ void conj_all(V (&v)[E]) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m].y = -v[m].y;
+}
+
 template <typename T> struct KCfg {
     // elements per thread: 16 complex64 or 8 complex128 in registers
     static constexpr int E_MAX = sizeof(T) == 4 ? 16 : 8;
@@ -138,6 +217,10 @@ template <typename T, int N> __host__ __device__ constexpr int threads_per_line(
 template <typename T, int N> __host__ __device__ constexpr int rows_per_block() {
     return threads_per_line<T, N>() >= 128 ? 1
            : (128 / threads_per_line<T, N>() > N ? N : 128 / threads_per_line<T, N>());
+}
+// minimum resident blocks per SM for a 64-register budget per thread
+template <int THREADS> __host__ __device__ constexpr int min_blocks() {
+    return THREADS >= 1024 ? 1 : (1024 / THREADS > 8 ? 8 : 1024 / THREADS);
 }
 // shared-memory stride between the lines a block holds; the extra offset
 // spreads lines that share a warp over different banks
@@ -151,7 +234,8 @@ template <typename T, int N, int LINES> __host__ __device__ constexpr int line_s
 // Row pass of the march: per row v = B_x S, screen, S = F_x U.  With DIAG the
 // block also reduces sum |U|^2 and max |U|^2 of its rows into partials.
 template <typename T, int N, bool DIAG>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>())
+__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
+                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
 k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>::type* __restrict__ tw,
            ScreenCoef<T> sc, double* __restrict__ partials) {
     using V = typename vec2<T>::type;
@@ -166,31 +250,41 @@ k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
     V v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = line[j + m * TL];
-    fft_stockham<V, N, E, true>(v, sm, tw, j);
     T tsum = (T)0, tmax = (T)0;
-    if (sc.active) {
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        if (half == 0) conj_all(v);
+        fft_stockham<V, N, E, false>(v, sm, tw, j);
+        if (half == 0) {
+            conj_all(v);  // v = B_x S: the field entering the screen
+            if (sc.active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc);
-    }
-    if constexpr (DIAG) {
+                for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc);
+            }
+            if constexpr (DIAG) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const T a = v[m].x * v[m].x + v[m].y * v[m].y;
-            tsum += a;
-            tmax = fmax(tmax, a);
+                for (int m = 0; m < E; ++m) {
+                    const T a = v[m].x * v[m].x + v[m].y * v[m].y;
+                    tsum += a;
+                    tmax = fmax(tmax, a);
+                }
+            }
         }
     }
-    fft_stockham<V, N, E, false>(v, sm, tw, j);
 #pragma unroll
     for (int m = 0; m < E; ++m) line[j + m * TL] = v[m];
     if constexpr (DIAG) block_partials<T>(tsum, tmax, partials);
 }
 
-// Column pass: per column kx, S <- B_y(P_x(kx) P_y(ky) F_y S); P_y carries 1/n^2.
+// Column pass: per column kx, S <- B_y(P_x(kx) P_y(ky) rot F_y S); P_y carries
+// 1/n^2 and rot = exp(i theta) is this step's global phase (see the march in
+// the host code: it decorrelates the FP32 rounding of the slowly rotating
+// spectral values from step to step).
 template <typename T, int N, int C>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * C)
+__global__ void __launch_bounds__(threads_per_line<T, N>() * C, min_blocks<threads_per_line<T, N>() * C>())
 k_col_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>::type* __restrict__ tw,
-           const typename tab_of<T>::type* __restrict__ px, const typename tab_of<T>::type* __restrict__ py) {
+           const typename tab_of<T>::type* __restrict__ px, const typename tab_of<T>::type* __restrict__ py,
+           typename tab_of<T>::type rot) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>();
     constexpr int LS = line_stride<T, N, C>();
@@ -202,18 +296,24 @@ k_col_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
     V v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = field[(size_t)(j + m * TL) * N + col];
-    fft_stockham<V, N, E, false>(v, sm, tw, j);
-    const auto pxc = __ldg(&px[col]);
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        fft_stockham<V, N, E, false>(v, sm, tw, j);
+        if (half == 0) {
+            const auto pxc = tabmul(__ldg(&px[col]), rot);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = twmul<false>(twmul<false>(v[m], pxc), __ldg(&py[j + m * TL]));
-    fft_stockham<V, N, E, true>(v, sm, tw, j);
+            for (int m = 0; m < E; ++m) v[m] = twmul<false>(twmul<false>(v[m], pxc), __ldg(&py[j + m * TL]));
+        }
+        conj_all(v);  // second round: conj(F_y(conj(.))) = B_y
+    }
 #pragma unroll
     for (int m = 0; m < E; ++m) field[(size_t)(j + m * TL) * N + col] = v[m];
 }
 
 // Forward row transform S = F_x U (load prologue); src may equal dst.
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>())
+__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
+                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
 k_row_forward(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
               const typename tab_of<T>::type* __restrict__ tw) {
     using V = typename vec2<T>::type;
@@ -234,10 +334,11 @@ k_row_forward(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
 // Readout: U = B_x S / n per row; reduces sum/max |U|^2 into partials and
 // optionally writes U (field_out) and |U|^2 (flu_out).
 template <typename T, int N>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>())
+__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
+                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
 k_readout(const typename vec2<T>::type* __restrict__ state, const typename tab_of<T>::type* __restrict__ tw,
           typename vec2<T>::type* __restrict__ field_out, T* __restrict__ flu_out,
-          double* __restrict__ partials) {
+          double* __restrict__ partials, typename vec2<T>::type unrot) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
     constexpr int LS = line_stride<T, N, RPB>();
@@ -257,7 +358,7 @@ k_readout(const typename vec2<T>::type* __restrict__ state, const typename tab_o
         const T a = v[m].x * v[m].x + v[m].y * v[m].y;
         tsum += a;
         tmax = fmax(tmax, a);
-        if (field_out) field_out[row * N + j + m * TL] = v[m];
+        if (field_out) field_out[row * N + j + m * TL] = cmul(v[m], unrot);  // remove the global phase
         if (flu_out) flu_out[row * N + j + m * TL] = a;
     }
     block_partials<T>(tsum, tmax, partials);

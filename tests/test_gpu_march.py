@@ -147,6 +147,45 @@ def test_fp32_kerr_only_power_drift_full_size():
     assert drift <= 1e-6, drift
 
 
+@pytest.mark.parametrize("terms", [configs.KERR, configs.KERR | configs.PLASMA | configs.MPA])
+def test_fp32_screen_against_exact_phase_up_to_large_phases(terms):
+    """Screen only (no diffraction), 20 cm step: the FP32 phase factor against the
+    oracle for per-step phases from ~0 to over 100 rad; the error allowed grows
+    with the phase as the FP32 rounding of the phase itself (eps * phase)."""
+    n = 256
+    cfg = configs.physics(n, 1.0, 70.0 if terms == configs.KERR else 20.0, terms)
+    rng = np.random.default_rng(9)
+    I = np.geomspace(1e9, 6e13, n * n)
+    rng.shuffle(I)
+    I = I.reshape(n, n)
+    v = np.sqrt(I) * np.exp(1j * rng.uniform(-np.pi, np.pi, (n, n)))
+    v = v.astype(np.complex64).astype(np.complex128)
+    Iv = np.abs(v) ** 2
+    ref = oracle.screen(v, cfg)
+    k0 = 2 * math.pi / cfg["lambda0"]
+    phi_k = k0 * cfg["n2"] * Iv * cfg["dz"]
+    phi_p = np.zeros_like(Iv)
+    mpa = np.zeros_like(Iv)
+    if terms & configs.PLASMA:
+        phi_p = (k0 * cfg["sigmaK"] * cfg["rho_nt"] * cfg["tau_pl"] / (2 * cfg["rho_c"])
+                 * Iv ** 8 * cfg["dz"])
+        mpa = cfg["betaK"] / 2 * Iv ** 7 * cfg["dz"]
+    assert (phi_k + phi_p).max() > 100
+    with Grid(cfg, precision="fp32") as g:
+        U = g.load(v).step(1).field().astype(np.complex128)
+    # FP32 error budget: |v|^2 carries ~3 roundings, so the Kerr phase has a
+    # relative error of a few eps; I^8 multiplies it by 8 for the plasma phase and
+    # I^7 by 7 for the absorption exponent.  The (idle) column pass also
+    # round-trips the field through FP32 FFTs, with an error relative to the
+    # field's rms rather than to each of its 250x-spread values (the field goes
+    # through four transforms in the two passes and one more in the readout).
+    eps = 2.0 ** -24
+    rms = float(np.sqrt(np.mean(Iv)))
+    err = np.abs(U - ref)
+    allowed = (1e-6 + 24 * eps * phi_k + 48 * eps * phi_p + 32 * eps * mpa) * np.abs(v) + 32 * eps * rms
+    assert np.all(err <= allowed), float(np.max(err / allowed))
+
+
 # -------------------------------------------------------------- readouts
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
