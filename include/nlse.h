@@ -198,6 +198,50 @@ nlse_status nlse_power_peak_noalloc(const void* field_dev, int32_t n, int32_t pr
 /* Release the handle (not the caller's workspace).  Synchronises. */
 nlse_status nlse_destroy(nlse_grid* g);
 
+/* ---------------------------------------------------------------- adjoint --
+ * Gradient of the fluence-mismatch loss of an M-step march,
+ *     J(theta, U0) = sum (|U_M|^2 - D)^2 / sum D^2,
+ * with respect to the six screen gains theta (Eq. 3 terms; see nlse_params)
+ * and the input field U0, by the exact discrete adjoint of the march (the
+ * paper fits its effective-lens ansatz with a genetic algorithm, Sec. 2 and
+ * Fig. 2; this makes the fit gradient-based).  Gradients follow the convention
+ * G = dJ/dRe + i dJ/dIm (PyTorch's for complex leaves).  The forward run keeps
+ * the state every ckpt_every steps; the backward sweep recomputes each segment
+ * from its checkpoint.  Memory: (2 + ckpt_every + ceil(M/ckpt_every)) fields
+ * plus one n x n double target (nlse_adjoint_workspace_size). */
+typedef struct nlse_adjoint nlse_adjoint;
+
+/* Device bytes for an adjoint of nsteps >= 1 steps checkpointed every
+ * ckpt_every >= 1 steps (values above nsteps act as nsteps).  No CUDA call. */
+nlse_status nlse_adjoint_workspace_size(const nlse_params* p, int32_t nsteps, int32_t ckpt_every,
+                                        size_t* bytes);
+
+/* Create on the current device; workspace as for nlse_create (256-byte aligned,
+ * caller-owned).  Uploads the propagator tables and their conjugates.  Synchronises. */
+nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ckpt_every, void* cuda_stream,
+                                void* dev_workspace, size_t workspace_bytes, nlse_adjoint** out);
+
+/* Replace the six screen gains (invalidates a pending forward run). */
+nlse_status nlse_adjoint_set_theta(nlse_adjoint* a, const double* theta);
+
+/* Target fluence D: n x n doubles (host or device), copied in; sum D^2 must be
+ * positive (NLSE_EINVAL otherwise).  Synchronises. */
+nlse_status nlse_adjoint_set_target(nlse_adjoint* a, const double* target, int on_device);
+
+/* March U0 (n x n interleaved complex of the grid precision, host or device)
+ * M steps with checkpoints, then evaluate J (FP64) into *loss and seed the
+ * adjoint.  NLSE_ESTATE without a target.  Synchronises. */
+nlse_status nlse_adjoint_forward(nlse_adjoint* a, const void* U0, int on_device, double* loss);
+
+/* Backward sweep after nlse_adjoint_forward: dtheta[6] (host) receives dJ/dtheta
+ * summed in FP64 in a fixed order; dU0 (n x n complex of the grid precision,
+ * host or device) receives dJ/dU0.  Consumes the forward run (NLSE_ESTATE if
+ * there is none).  Synchronises. */
+nlse_status nlse_adjoint_backward(nlse_adjoint* a, double* dtheta, void* dU0, int dU0_on_device);
+
+/* Release the handle (not the workspace).  Synchronises. */
+nlse_status nlse_adjoint_destroy(nlse_adjoint* a);
+
 #ifdef __cplusplus
 }
 #endif

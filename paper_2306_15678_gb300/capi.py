@@ -71,6 +71,17 @@ _SIGS = {
     "nlse_power_peak_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "nlse_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_adjoint_workspace_size": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.POINTER(ctypes.c_size_t)]),
+    "nlse_adjoint_create": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "nlse_adjoint_set_theta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "nlse_adjoint_set_target": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_adjoint_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "nlse_adjoint_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_adjoint_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -187,3 +198,44 @@ def nlse_power_peak_noalloc(field_dev: int, n: int, precision: int, L: float, st
 
 def nlse_destroy(h) -> None:
     check(lib().nlse_destroy(h), "nlse_destroy")
+
+
+def nlse_adjoint_workspace_size(p: nlse_params, nsteps: int, ckpt: int) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().nlse_adjoint_workspace_size(ctypes.byref(p), int(nsteps), int(ckpt), ctypes.byref(b)),
+          "nlse_adjoint_workspace_size")
+    return int(b.value)
+
+
+def nlse_adjoint_create(p: nlse_params, nsteps: int, ckpt: int, stream: int, workspace: int,
+                        nbytes: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    check(lib().nlse_adjoint_create(ctypes.byref(p), int(nsteps), int(ckpt), ctypes.c_void_p(stream),
+                                    ctypes.c_void_p(workspace), ctypes.c_size_t(nbytes), ctypes.byref(h)),
+          "nlse_adjoint_create")
+    return h
+
+
+def nlse_adjoint_set_theta(h, theta_ptr: int) -> None:
+    check(lib().nlse_adjoint_set_theta(h, ctypes.c_void_p(theta_ptr)), "nlse_adjoint_set_theta")
+
+
+def nlse_adjoint_set_target(h, target: int, on_device: bool) -> None:
+    check(lib().nlse_adjoint_set_target(h, ctypes.c_void_p(target), int(bool(on_device))),
+          "nlse_adjoint_set_target")
+
+
+def nlse_adjoint_forward(h, src: int, on_device: bool) -> float:
+    v = ctypes.c_double(0)
+    check(lib().nlse_adjoint_forward(h, ctypes.c_void_p(src), int(bool(on_device)), ctypes.byref(v)),
+          "nlse_adjoint_forward")
+    return float(v.value)
+
+
+def nlse_adjoint_backward(h, dtheta_ptr: int, dU0: int, on_device: bool) -> None:
+    check(lib().nlse_adjoint_backward(h, ctypes.c_void_p(dtheta_ptr), ctypes.c_void_p(dU0),
+                                      int(bool(on_device))), "nlse_adjoint_backward")
+
+
+def nlse_adjoint_destroy(h) -> None:
+    check(lib().nlse_adjoint_destroy(h), "nlse_adjoint_destroy")

@@ -260,12 +260,12 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const double th = step_phase(g->steps + 1);
-        cudaError_t e = ks->col_pass(field, tw, px, py, rot_entry<T>(th), g->cols, g->stream);
+        cudaError_t e = ks->col_pass(field, field, tw, px, py, rot_entry<T>(th), g->cols, g->stream);
         g->theta = std::fmod(g->theta + th, kTwoPi);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 1], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const bool diag = g->p.diag_every > 0 && ((g->steps + 1) % g->p.diag_every) == 0;
-        e = ks->row_pass(field, tw, Sel<T>::sc(g), partials, diag, g->stream);
+        e = ks->row_pass(field, field, tw, Sel<T>::sc(g), partials, diag, g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (diag) {
             double* slot = dat(g, g->lay.hist) + 2 * (g->hist_count % kHistCap);
@@ -585,6 +585,318 @@ nlse_status nlse_destroy(nlse_grid* g) {
     if (!g) return NLSE_EINVAL;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     delete g;
+    return cuerr(e);
+}
+
+}  // extern "C"
+
+// ================================================================ adjoint ==
+// Reverse-mode gradient of J = sum (|U_M|^2 - D)^2 / sum D^2 after M steps
+// (kernels in adjoint.cuh).  The forward run stores the x-spectral state S
+// every `ckpt` steps; the backward sweep recomputes each segment from its
+// checkpoint, keeping the column-pass outputs T_n of the segment, and then
+// runs the backward row and column passes from the last step of the segment
+// to its first.  All kernels are deterministic, so the recomputed states are
+// bit-identical to the forward ones.
+
+namespace {
+
+struct AdjLayout {
+    size_t state, gam, tw, px, py, pxc, pyc, seg, ckpt, target, partials, acc, result, total;
+    int nck;
+};
+
+AdjLayout adj_layout_for(int n, int precision, int nsteps, int ckpt) {
+    const size_t cs = precision == NLSE_FP64 ? 16 : 8;
+    const size_t field = (size_t)n * n * cs;
+    AdjLayout L;
+    L.nck = (nsteps + ckpt - 1) / ckpt;
+    if (L.nck < 1) L.nck = 1;
+    size_t o = 0;
+    L.state = o;    o = align256(o + field);
+    L.gam = o;      o = align256(o + field);
+    L.tw = o;       o = align256(o + (size_t)n * 16);
+    L.px = o;       o = align256(o + (size_t)n * 16);
+    L.py = o;       o = align256(o + (size_t)n * 16);
+    L.pxc = o;      o = align256(o + (size_t)n * 16);
+    L.pyc = o;      o = align256(o + (size_t)n * 16);
+    L.seg = o;      o = align256(o + field * (size_t)ckpt);
+    L.ckpt = o;     o = align256(o + field * (size_t)L.nck);
+    L.target = o;   o = align256(o + (size_t)n * n * sizeof(double));
+    L.partials = o; o = align256(o + (size_t)n * 2 * sizeof(double));
+    L.acc = o;      o = align256(o + (size_t)n * 6 * sizeof(double));
+    L.result = o;   o = align256(o + 4 * sizeof(double) + sizeof(int));
+    L.total = o;
+    return L;
+}
+
+template <typename T> AdjCoef<T> adj_coef(const nlse_params* p) {
+    AdjCoef<T> a;
+    a.sc = screen_coef<T>(p);
+    const double k0 = kTwoPi * p->n0 / p->lambda0;
+    const double eps_k = 2.0 * k0 * k0 * p->n2 / p->n0;
+    const double eps_m = -k0 * k0 * p->sigmaK * p->rho_nt * p->tau_pl / p->rho_c;
+    a.aK = (T)((p->terms & NLSE_KERR) ? p->dz * eps_k / (2.0 * k0) * kIref : 0.0);
+    a.aP = (T)((p->terms & NLSE_PLASMA) ? p->dz * eps_m / (2.0 * k0) * std::pow(kIref, (double)p->K) : 0.0);
+    a.aA = (T)((p->terms & NLSE_MPA) ? p->dz * (-p->betaK) / 2.0 * std::pow(kIref, (double)(p->K - 1)) : 0.0);
+    return a;
+}
+
+}  // namespace
+
+struct nlse_adjoint {
+    nlse_params p;
+    int32_t nsteps, ckpt;
+    cudaStream_t stream;
+    unsigned char* ws;
+    AdjLayout lay;
+    int cols;
+    const KernelSet<float>* k32;
+    const KernelSet<double>* k64;
+    AdjCoef<float> ac32;
+    AdjCoef<double> ac64;
+    double sum_d2;
+    int have_target, have_forward;
+};
+
+namespace {
+
+template <typename T> struct ASel;
+template <> struct ASel<float> {
+    static const KernelSet<float>* ks(const nlse_adjoint* a) { return a->k32; }
+    static const AdjCoef<float>& ac(const nlse_adjoint* a) { return a->ac32; }
+};
+template <> struct ASel<double> {
+    static const KernelSet<double>* ks(const nlse_adjoint* a) { return a->k64; }
+    static const AdjCoef<double>& ac(const nlse_adjoint* a) { return a->ac64; }
+};
+
+template <typename T> VT<T>* aat(nlse_adjoint* a, size_t off) { return reinterpret_cast<VT<T>*>(a->ws + off); }
+template <typename T> const WT<T>* atab(nlse_adjoint* a, size_t off) {
+    return reinterpret_cast<const WT<T>*>(a->ws + off);
+}
+inline size_t adj_field_bytes(const nlse_adjoint* a) {
+    return (size_t)a->p.n * a->p.n * (a->p.precision == NLSE_FP64 ? 16 : 8);
+}
+
+template <typename T> nlse_status adj_upload(nlse_adjoint* a) {
+    std::vector<double> px, py, tw;
+    propagator_tables(&a->p, px, py);
+    const int ept = std::min(a->p.n, sizeof(T) == 4 ? 16 : 8);
+    twiddle_table(a->p.n, ept, tw);
+    std::vector<double> pxc(px), pyc(py);
+    for (size_t i = 1; i < pxc.size(); i += 2) { pxc[i] = -pxc[i]; pyc[i] = -pyc[i]; }
+    const std::vector<double>* src[5] = {&tw, &px, &py, &pxc, &pyc};
+    const size_t off[5] = {a->lay.tw, a->lay.px, a->lay.py, a->lay.pxc, a->lay.pyc};
+    for (int t = 0; t < 5; ++t) {
+        std::vector<T> r;
+        round_table(*src[t], r);
+        if (cudaMemcpyAsync(a->ws + off[t], r.data(), r.size() * sizeof(T), cudaMemcpyHostToDevice,
+                            a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
+    }
+    return NLSE_OK;
+}
+
+template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* src, int on_device, double* loss) {
+    const KernelSet<T>* ks = ASel<T>::ks(a);
+    VT<T>* state = aat<T>(a, a->lay.state);
+    const WT<T>* tw = atab<T>(a, a->lay.tw);
+    const size_t fb = adj_field_bytes(a);
+    cudaError_t e;
+    if (on_device) {
+        e = ks->row_forward((const VT<T>*)src, state, tw, a->stream);
+    } else {
+        e = cudaMemcpyAsync(state, src, fb, cudaMemcpyHostToDevice, a->stream);
+        if (e == cudaSuccess) e = ks->row_forward(state, state, tw, a->stream);
+    }
+    if (e != cudaSuccess) return NLSE_ECUDA;
+    const ScreenCoef<T>& sc = ASel<T>::ac(a).sc;
+    double* partials = reinterpret_cast<double*>(a->ws + a->lay.partials);
+    for (int s = 0; s < a->nsteps; ++s) {
+        if (s % a->ckpt == 0 &&
+            cudaMemcpyAsync(a->ws + a->lay.ckpt + fb * (size_t)(s / a->ckpt), state, fb,
+                            cudaMemcpyDeviceToDevice, a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        if (ks->col_pass(state, state, tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
+                         rot_entry<T>(step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        if (ks->row_pass(state, state, tw, sc, partials, false, a->stream) != cudaSuccess) return NLSE_ECUDA;
+    }
+    double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
+    if (ks->loss_seed(state, aat<T>(a, a->lay.gam), reinterpret_cast<const double*>(a->ws + a->lay.target),
+                      tw, 1.0 / a->sum_d2, partials, a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    k_finalize<<<1, 256, 0, a->stream>>>(partials, ks->row_blocks, 1.0 / a->sum_d2, result,
+                                         reinterpret_cast<int*>(result + 4));
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    double r[2];
+    if (cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
+    *loss = r[0];
+    return std::isfinite(r[0]) ? NLSE_OK : NLSE_ENONFINITE;
+}
+
+template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dtheta, void* dU0, int on_device) {
+    const KernelSet<T>* ks = ASel<T>::ks(a);
+    const AdjCoef<T>& ac = ASel<T>::ac(a);
+    VT<T>* state = aat<T>(a, a->lay.state);
+    VT<T>* gam = aat<T>(a, a->lay.gam);
+    const WT<T>* tw = atab<T>(a, a->lay.tw);
+    const size_t fb = adj_field_bytes(a);
+    double* partials = reinterpret_cast<double*>(a->ws + a->lay.partials);
+    double* acc = reinterpret_cast<double*>(a->ws + a->lay.acc);
+    if (cudaMemsetAsync(acc, 0, (size_t)a->p.n * 6 * sizeof(double), a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    auto seg = [&](int i) { return reinterpret_cast<VT<T>*>(a->ws + a->lay.seg + fb * (size_t)i); };
+    for (int c = (a->nsteps - 1) / a->ckpt; c >= 0; --c) {
+        const int c0 = c * a->ckpt, c1 = std::min(c0 + a->ckpt, (int)a->nsteps);
+        if (cudaMemcpyAsync(state, a->ws + a->lay.ckpt + fb * (size_t)c, fb, cudaMemcpyDeviceToDevice,
+                            a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+        for (int s = c0; s < c1; ++s) {  // recompute the segment, keeping T_s
+            if (ks->col_pass(state, seg(s - c0), tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
+                             rot_entry<T>(step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+                return NLSE_ECUDA;
+            if (s + 1 < c1 &&
+                ks->row_pass(seg(s - c0), state, tw, ac.sc, partials, false, a->stream) != cudaSuccess)
+                return NLSE_ECUDA;
+        }
+        for (int s = c1 - 1; s >= c0; --s) {  // reverse the segment
+            if (ks->adj_row(gam, seg(s - c0), tw, ac, acc, a->stream) != cudaSuccess) return NLSE_ECUDA;
+            if (ks->col_pass(gam, gam, tw, atab<T>(a, a->lay.pxc), atab<T>(a, a->lay.pyc),
+                             rot_entry<T>(-step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+                return NLSE_ECUDA;
+        }
+    }
+    // dJ/dU0 = B_x G_S0 (the readout applies 1/n, undone by the factor n)
+    VT<T> scale;
+    scale.x = (T)a->p.n;
+    scale.y = (T)0;
+    VT<T>* out = on_device ? (VT<T>*)dU0 : seg(0);
+    if (ks->readout(gam, tw, out, nullptr, partials, scale, a->stream) != cudaSuccess) return NLSE_ECUDA;
+    std::vector<double> h((size_t)a->p.n * 6);
+    if (cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, a->stream) !=
+        cudaSuccess)
+        return NLSE_ECUDA;
+    if (!on_device &&
+        cudaMemcpyAsync(dU0, out, fb, cudaMemcpyDeviceToHost, a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
+    for (int q = 0; q < 6; ++q) dtheta[q] = 0.0;
+    for (int b = 0; b < ks->row_blocks; ++b)  // fixed order: deterministic
+        for (int q = 0; q < 6; ++q) dtheta[q] += h[6 * (size_t)b + q];
+    return NLSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlse_status nlse_adjoint_workspace_size(const nlse_params* p, int32_t nsteps, int32_t ckpt_every,
+                                        size_t* bytes) {
+    if (!bytes || nsteps < 1 || ckpt_every < 1) return NLSE_EINVAL;
+    nlse_status st = validate(p);
+    if (st != NLSE_OK) return st;
+    *bytes = adj_layout_for(p->n, p->precision, nsteps, std::min(ckpt_every, nsteps)).total;
+    return NLSE_OK;
+}
+
+nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ckpt_every, void* cuda_stream,
+                                void* dev_workspace, size_t workspace_bytes, nlse_adjoint** out) {
+    if (!out || !dev_workspace || nsteps < 1 || ckpt_every < 1) return NLSE_EINVAL;
+    *out = nullptr;
+    nlse_status st = validate(p);
+    if (st != NLSE_OK) return st;
+    if (reinterpret_cast<uintptr_t>(dev_workspace) & 255) return NLSE_EINVAL;
+    const int ck = std::min(ckpt_every, nsteps);
+    AdjLayout lay = adj_layout_for(p->n, p->precision, nsteps, ck);
+    if (workspace_bytes < lay.total) return NLSE_ENOMEM;
+    nlse_adjoint* a = new (std::nothrow) nlse_adjoint();
+    if (!a) return NLSE_ENOMEM;
+    a->p = *p;
+    a->nsteps = nsteps;
+    a->ckpt = ck;
+    a->stream = static_cast<cudaStream_t>(cuda_stream);
+    a->ws = static_cast<unsigned char*>(dev_workspace);
+    a->lay = lay;
+    const int k = log2_exact(p->n);
+    if (p->precision == NLSE_FP64) {
+        a->k64 = kernels_f64(k);
+        a->cols = a->k64->col_default;
+        a->ac64 = adj_coef<double>(p);
+        st = adj_upload<double>(a);
+    } else {
+        a->k32 = kernels_f32(k);
+        a->cols = a->k32->col_default;
+        a->ac32 = adj_coef<float>(p);
+        st = adj_upload<float>(a);
+    }
+    if (st != NLSE_OK) { delete a; return st; }
+    *out = a;
+    return NLSE_OK;
+}
+
+nlse_status nlse_adjoint_set_theta(nlse_adjoint* a, const double* theta) {
+    if (!a || !theta) return NLSE_EINVAL;
+    nlse_params q = a->p;
+    for (int i = 0; i < 6; ++i) q.theta[i] = theta[i];
+    nlse_status st = validate(&q);
+    if (st != NLSE_OK) return st;
+    a->p = q;
+    if (a->p.precision == NLSE_FP64) a->ac64 = adj_coef<double>(&a->p);
+    else a->ac32 = adj_coef<float>(&a->p);
+    a->have_forward = 0;
+    return NLSE_OK;
+}
+
+nlse_status nlse_adjoint_set_target(nlse_adjoint* a, const double* target, int on_device) {
+    if (!a || !target) return NLSE_EINVAL;
+    const int n = a->p.n;
+    const size_t bytes = (size_t)n * n * sizeof(double);
+    double* d = reinterpret_cast<double*>(a->ws + a->lay.target);
+    if (cudaMemcpyAsync(d, target, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    double* partials = reinterpret_cast<double*>(a->ws + a->lay.partials);
+    double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
+    k_sumsq_rows<<<n, 256, 0, a->stream>>>(d, n, partials);
+    k_finalize<<<1, 256, 0, a->stream>>>(partials, n, 1.0, result, reinterpret_cast<int*>(result + 4));
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    double r[2];
+    if (cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, a->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
+    if (!(r[0] > 0.0) || !std::isfinite(r[0])) return NLSE_EINVAL;  // an all-zero target has no loss scale
+    a->sum_d2 = r[0];
+    a->have_target = 1;
+    a->have_forward = 0;
+    return NLSE_OK;
+}
+
+nlse_status nlse_adjoint_forward(nlse_adjoint* a, const void* U0, int on_device, double* loss) {
+    if (!a || !U0 || !loss) return NLSE_EINVAL;
+    if (!a->have_target) return NLSE_ESTATE;
+    nlse_status st = a->p.precision == NLSE_FP64 ? adj_forward_impl<double>(a, U0, on_device, loss)
+                                                 : adj_forward_impl<float>(a, U0, on_device, loss);
+    a->have_forward = st == NLSE_OK;
+    return st;
+}
+
+nlse_status nlse_adjoint_backward(nlse_adjoint* a, double* dtheta, void* dU0, int dU0_on_device) {
+    if (!a || !dtheta || !dU0) return NLSE_EINVAL;
+    if (!a->have_forward) return NLSE_ESTATE;
+    a->have_forward = 0;  // the backward sweep consumes the seeded adjoint state
+    return a->p.precision == NLSE_FP64 ? adj_backward_impl<double>(a, dtheta, dU0, dU0_on_device)
+                                       : adj_backward_impl<float>(a, dtheta, dU0, dU0_on_device);
+}
+
+nlse_status nlse_adjoint_destroy(nlse_adjoint* a) {
+    if (!a) return NLSE_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(a->stream);
+    delete a;
     return cuerr(e);
 }
 

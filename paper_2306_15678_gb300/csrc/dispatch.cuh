@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "adjoint.cuh"
 #include "kernels.cuh"
 
 namespace nlse {
@@ -17,13 +18,16 @@ template <typename T> struct KernelSet {
     int row_blocks;    // blocks of the row-oriented kernels (n / rows_per_block)
     int col_mask;      // bit i set: column tile kColOptions[i] is instantiated
     int col_default;   // default column tile
-    cudaError_t (*row_pass)(V* field, const W* tw, ScreenCoef<T> sc, double* partials, bool diag,
-                            cudaStream_t s);
-    cudaError_t (*col_pass)(V* field, const W* tw, const W* px, const W* py, W rot, int cols,
-                            cudaStream_t s);
+    cudaError_t (*row_pass)(const V* src, V* dst, const W* tw, ScreenCoef<T> sc, double* partials,
+                            bool diag, cudaStream_t s);
+    cudaError_t (*col_pass)(const V* src, V* dst, const W* tw, const W* px, const W* py, W rot,
+                            int cols, cudaStream_t s);
     cudaError_t (*row_forward)(const V* src, V* dst, const W* tw, cudaStream_t s);
     cudaError_t (*readout)(const V* state, const W* tw, V* field_out, T* flu_out, double* partials,
                            V unrot, cudaStream_t s);
+    cudaError_t (*loss_seed)(const V* state, V* gam, const double* target, const W* tw,
+                             double seed_scale, double* partials, cudaStream_t s);
+    cudaError_t (*adj_row)(V* gam, const V* tn, const W* tw, AdjCoef<T> ac, double* acc, cudaStream_t s);
 };
 
 // Raise the dynamic shared-memory limit of one kernel once per device.  The
@@ -53,30 +57,32 @@ template <typename T, int N, int C> constexpr bool col_valid() {
 }
 
 template <typename T, int N>
-cudaError_t launch_row_pass(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
-                            ScreenCoef<T> sc, double* partials, bool diag, cudaStream_t s) {
+cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                            const typename tab_of<T>::type* tw, ScreenCoef<T> sc, double* partials,
+                            bool diag, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
     cudaError_t e;
     if (diag) {
         if ((e = ensure_smem<k_row_pass<T, N, true>>(SMEM)) != cudaSuccess) return e;
-        k_row_pass<T, N, true><<<N / RPB, THREADS, SMEM, s>>>(field, tw, sc, partials);
+        k_row_pass<T, N, true><<<N / RPB, THREADS, SMEM, s>>>(src, dst, tw, sc, partials);
     } else {
         if ((e = ensure_smem<k_row_pass<T, N, false>>(SMEM)) != cudaSuccess) return e;
-        k_row_pass<T, N, false><<<N / RPB, THREADS, SMEM, s>>>(field, tw, sc, partials);
+        k_row_pass<T, N, false><<<N / RPB, THREADS, SMEM, s>>>(src, dst, tw, sc, partials);
     }
     return cudaGetLastError();
 }
 
 template <typename T, int N, int C>
-cudaError_t launch_col_c(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
+cudaError_t launch_col_c(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                         const typename tab_of<T>::type* tw,
                          const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
                          typename tab_of<T>::type rot, cudaStream_t s) {
     if constexpr (col_valid<T, N, C>()) {
         constexpr int SMEM = col_smem_bytes<T, N, C>();
         cudaError_t e = ensure_smem<k_col_pass<T, N, C>>(SMEM);
         if (e != cudaSuccess) return e;
-        k_col_pass<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(field, tw, px, py, rot);
+        k_col_pass<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(src, dst, tw, px, py, rot);
         return cudaGetLastError();
     } else {
         return cudaErrorInvalidConfiguration;
@@ -84,15 +90,16 @@ cudaError_t launch_col_c(typename vec2<T>::type* field, const typename tab_of<T>
 }
 
 template <typename T, int N>
-cudaError_t launch_col_pass(typename vec2<T>::type* field, const typename tab_of<T>::type* tw,
+cudaError_t launch_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                            const typename tab_of<T>::type* tw,
                             const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
                             typename tab_of<T>::type rot, int cols, cudaStream_t s) {
     switch (cols) {
-        case 1: return launch_col_c<T, N, 1>(field, tw, px, py, rot, s);
-        case 2: return launch_col_c<T, N, 2>(field, tw, px, py, rot, s);
-        case 4: return launch_col_c<T, N, 4>(field, tw, px, py, rot, s);
-        case 8: return launch_col_c<T, N, 8>(field, tw, px, py, rot, s);
-        case 16: return launch_col_c<T, N, 16>(field, tw, px, py, rot, s);
+        case 1: return launch_col_c<T, N, 1>(src, dst, tw, px, py, rot, s);
+        case 2: return launch_col_c<T, N, 2>(src, dst, tw, px, py, rot, s);
+        case 4: return launch_col_c<T, N, 4>(src, dst, tw, px, py, rot, s);
+        case 8: return launch_col_c<T, N, 8>(src, dst, tw, px, py, rot, s);
+        case 16: return launch_col_c<T, N, 16>(src, dst, tw, px, py, rot, s);
         default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -117,6 +124,29 @@ cudaError_t launch_readout(const typename vec2<T>::type* state, const typename t
     cudaError_t e = ensure_smem<k_readout<T, N>>(SMEM);
     if (e != cudaSuccess) return e;
     k_readout<T, N><<<N / RPB, THREADS, SMEM, s>>>(state, tw, field_out, flu_out, partials, unrot);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_loss_seed(const typename vec2<T>::type* state, typename vec2<T>::type* gam,
+                             const double* target, const typename tab_of<T>::type* tw, double seed_scale,
+                             double* partials, cudaStream_t s) {
+    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
+    constexpr int SMEM = row_smem_bytes<T, N>();
+    cudaError_t e = ensure_smem<k_loss_seed<T, N>>(SMEM);
+    if (e != cudaSuccess) return e;
+    k_loss_seed<T, N><<<N / RPB, THREADS, SMEM, s>>>(state, gam, target, tw, seed_scale, partials);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_adj_row(typename vec2<T>::type* gam, const typename vec2<T>::type* tn,
+                           const typename tab_of<T>::type* tw, AdjCoef<T> ac, double* acc, cudaStream_t s) {
+    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
+    constexpr int SMEM = row_smem_bytes<T, N>();
+    cudaError_t e = ensure_smem<k_adj_row<T, N>>(SMEM);
+    if (e != cudaSuccess) return e;
+    k_adj_row<T, N><<<N / RPB, THREADS, SMEM, s>>>(gam, tn, tw, ac, acc);
     return cudaGetLastError();
 }
 
@@ -154,6 +184,8 @@ template <typename T, int N> KernelSet<T> make_set() {
     k.col_pass = &launch_col_pass<T, N>;
     k.row_forward = &launch_row_forward<T, N>;
     k.readout = &launch_readout<T, N>;
+    k.loss_seed = &launch_loss_seed<T, N>;
+    k.adj_row = &launch_adj_row<T, N>;
     return k;
 }
 

@@ -236,8 +236,8 @@ template <typename T, int N, int LINES> __host__ __device__ constexpr int line_s
 template <typename T, int N, bool DIAG>
 __global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
                                   min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
-k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>::type* __restrict__ tw,
-           ScreenCoef<T> sc, double* __restrict__ partials) {
+k_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+           const typename tab_of<T>::type* __restrict__ tw, ScreenCoef<T> sc, double* __restrict__ partials) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
     constexpr int LS = line_stride<T, N, RPB>();
@@ -245,7 +245,7 @@ k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
     V* smem = reinterpret_cast<V*>(smraw);
     const int g = threadIdx.x / TL, j = threadIdx.x % TL;
     const int row = blockIdx.x * RPB + g;
-    V* line = field + (size_t)row * N;
+    const V* line = src + (size_t)row * N;
     V* sm = smem + g * LS;
     V v[E];
 #pragma unroll
@@ -271,8 +271,9 @@ k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
             }
         }
     }
+    V* out = dst + (size_t)row * N;
 #pragma unroll
-    for (int m = 0; m < E; ++m) line[j + m * TL] = v[m];
+    for (int m = 0; m < E; ++m) out[j + m * TL] = v[m];
     if constexpr (DIAG) block_partials<T>(tsum, tmax, partials);
 }
 
@@ -282,7 +283,8 @@ k_row_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
 // spectral values from step to step).
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(threads_per_line<T, N>() * C, min_blocks<threads_per_line<T, N>() * C>())
-k_col_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>::type* __restrict__ tw,
+k_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+           const typename tab_of<T>::type* __restrict__ tw,
            const typename tab_of<T>::type* __restrict__ px, const typename tab_of<T>::type* __restrict__ py,
            typename tab_of<T>::type rot) {
     using V = typename vec2<T>::type;
@@ -295,7 +297,7 @@ k_col_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
     V* sm = smem + c * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = field[(size_t)(j + m * TL) * N + col];
+    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(j + m * TL) * N + col];
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         fft_stockham<V, N, E, false>(v, sm, tw, j);
@@ -307,7 +309,7 @@ k_col_pass(typename vec2<T>::type* __restrict__ field, const typename tab_of<T>:
         conj_all(v);  // second round: conj(F_y(conj(.))) = B_y
     }
 #pragma unroll
-    for (int m = 0; m < E; ++m) field[(size_t)(j + m * TL) * N + col] = v[m];
+    for (int m = 0; m < E; ++m) dst[(size_t)(j + m * TL) * N + col] = v[m];
 }
 
 // Forward row transform S = F_x U (load prologue); src may equal dst.
