@@ -141,6 +141,11 @@ nlse_status nlse_step(nlse_grid* g, int32_t nsteps);
  * for the per-kernel roofline; the paper has no counterpart. */
 nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double* row_ms);
 
+/* Column-tile width of the column pass (1, 2, 4, 8 or 16 columns per block;
+ * NLSE_EUNSUPPORTED for a width this size cannot use).  Chosen by the
+ * autotuner; results do not depend on it. */
+nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols);
+
 /* Number of z steps taken since the last load. */
 nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps);
 
@@ -197,6 +202,65 @@ nlse_status nlse_power_peak_noalloc(const void* field_dev, int32_t n, int32_t pr
 
 /* Release the handle (not the caller's workspace).  Synchronises. */
 nlse_status nlse_destroy(nlse_grid* g);
+
+/* ------------------------------------------------------------------ batch --
+ * Many independent beams (the paper's statistical realisations, Sec. 3.3, and
+ * test beams, Sec. 2) of different grid sizes (n = 256..4096, FP32 only)
+ * marched together: every z step of every beam runs inside one persistent
+ * kernel launch whose blocks pull (step, pass, beam, tile) work items in
+ * dependency order.  Waits between items are bounded (timeout_ms); when one
+ * runs out the launch stops and nlse_batch_status reports NLSE_ETIMEOUT.  A
+ * batched beam is bit-identical to the same beam on its own nlse_grid. */
+typedef struct nlse_batch nlse_batch;
+
+/* Launch shape of the persistent kernel (chosen by an autotuner; see the
+ * Python package).  threads: 256 or 512 threads per block (sets the rows and
+ * columns per tile); ctas_per_sm: resident blocks per SM (0 = as many as fit);
+ * timeout_ms: bound on every wait; debug_skip_item: test hook -- the work item
+ * with this index never reports completion (-1 = none). */
+typedef struct nlse_batch_tuning {
+    int32_t threads;
+    int32_t ctas_per_sm;
+    int32_t timeout_ms;
+    int64_t debug_skip_item;
+} nlse_batch_tuning;
+
+/* Device bytes for `count` beams with parameters params[0..count-1].  No CUDA call. */
+nlse_status nlse_batch_workspace_size(int32_t count, const nlse_params* params, size_t* bytes);
+
+/* Create (tuning may be NULL for the defaults 256, 0, 2000, -1).  Builds every
+ * beam's tables exactly as nlse_create does.  Synchronises. */
+nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nlse_batch_tuning* tuning,
+                              void* cuda_stream, void* dev_workspace, size_t workspace_bytes,
+                              nlse_batch** out);
+
+/* Load beam `beam`'s field (n x n complex64, host or device) before any step. */
+nlse_status nlse_batch_load_field(nlse_batch* b, int32_t beam, const void* src, int src_on_device);
+
+/* Advance every beam nsteps Lie steps in one persistent launch (async). */
+nlse_status nlse_batch_step(nlse_batch* b, int32_t nsteps);
+
+/* Capture the launch of nsteps steps into a CUDA graph (counter resets,
+ * persistent kernel, step-base update) for nlse_batch_replay. */
+nlse_status nlse_batch_capture(nlse_batch* b, int32_t nsteps);
+
+/* Launch the captured graph: every beam advances the captured step count. */
+nlse_status nlse_batch_replay(nlse_batch* b);
+
+/* Read and clear the status word (synchronises): NLSE_OK or NLSE_ETIMEOUT. */
+nlse_status nlse_batch_status(nlse_batch* b);
+
+/* Steps taken by every beam since creation. */
+nlse_status nlse_batch_steps_taken(nlse_batch* b, int64_t* steps);
+
+/* Field of one beam (n x n complex64) to dst (host if dst_on_device == 0). */
+nlse_status nlse_batch_read_field(nlse_batch* b, int32_t beam, void* dst, int dst_on_device);
+
+/* Power sum |U|^2 dx^2 of one beam, FP64, deterministic.  Synchronises. */
+nlse_status nlse_batch_power(nlse_batch* b, int32_t beam, double* watts);
+
+/* Release the handle (not the workspace).  Synchronises. */
+nlse_status nlse_batch_destroy(nlse_batch* b);
 
 /* ---------------------------------------------------------------- adjoint --
  * Gradient of the fluence-mismatch loss of an M-step march,

@@ -40,6 +40,15 @@ class nlse_params(ctypes.Structure):
     ]
 
 
+class nlse_batch_tuning(ctypes.Structure):
+    _fields_ = [
+        ("threads", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("timeout_ms", ctypes.c_int32),
+        ("debug_skip_item", ctypes.c_int64),
+    ]
+
+
 class NlseError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = int(status)
@@ -71,6 +80,19 @@ _SIGS = {
     "nlse_power_peak_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     "nlse_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_batch_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "nlse_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "nlse_batch_load_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "nlse_batch_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "nlse_batch_replay": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_batch_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_batch_steps_taken": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "nlse_batch_read_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_batch_power": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "nlse_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nlse_set_column_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "nlse_adjoint_workspace_size": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.POINTER(ctypes.c_size_t)]),
     "nlse_adjoint_create": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
@@ -239,3 +261,75 @@ def nlse_adjoint_backward(h, dtheta_ptr: int, dU0: int, on_device: bool) -> None
 
 def nlse_adjoint_destroy(h) -> None:
     check(lib().nlse_adjoint_destroy(h), "nlse_adjoint_destroy")
+
+
+def nlse_set_column_tile(h, cols: int) -> None:
+    check(lib().nlse_set_column_tile(h, int(cols)), "nlse_set_column_tile")
+
+
+def _params_array(params):
+    arr = (nlse_params * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p
+    return arr
+
+
+def nlse_batch_workspace_size(params) -> int:
+    arr = _params_array(params)
+    b = ctypes.c_size_t(0)
+    check(lib().nlse_batch_workspace_size(len(params), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(b)),
+          "nlse_batch_workspace_size")
+    return int(b.value)
+
+
+def nlse_batch_create(params, tuning, stream: int, workspace: int, nbytes: int) -> ctypes.c_void_p:
+    arr = _params_array(params)
+    h = ctypes.c_void_p()
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    check(lib().nlse_batch_create(len(params), ctypes.cast(arr, ctypes.c_void_p),
+                                  ctypes.cast(tp, ctypes.c_void_p) if tp is not None else None,
+                                  ctypes.c_void_p(stream), ctypes.c_void_p(workspace), ctypes.c_size_t(nbytes),
+                                  ctypes.byref(h)), "nlse_batch_create")
+    return h
+
+
+def nlse_batch_load_field(h, beam: int, src: int, on_device: bool) -> None:
+    check(lib().nlse_batch_load_field(h, int(beam), ctypes.c_void_p(src), int(bool(on_device))),
+          "nlse_batch_load_field")
+
+
+def nlse_batch_step(h, nsteps: int) -> None:
+    check(lib().nlse_batch_step(h, int(nsteps)), "nlse_batch_step")
+
+
+def nlse_batch_capture(h, nsteps: int) -> None:
+    check(lib().nlse_batch_capture(h, int(nsteps)), "nlse_batch_capture")
+
+
+def nlse_batch_replay(h) -> None:
+    check(lib().nlse_batch_replay(h), "nlse_batch_replay")
+
+
+def nlse_batch_status(h) -> int:
+    return int(lib().nlse_batch_status(h))
+
+
+def nlse_batch_steps_taken(h) -> int:
+    v = ctypes.c_int64(0)
+    check(lib().nlse_batch_steps_taken(h, ctypes.byref(v)), "nlse_batch_steps_taken")
+    return int(v.value)
+
+
+def nlse_batch_read_field(h, beam: int, dst: int, on_device: bool) -> None:
+    check(lib().nlse_batch_read_field(h, int(beam), ctypes.c_void_p(dst), int(bool(on_device))),
+          "nlse_batch_read_field")
+
+
+def nlse_batch_power(h, beam: int) -> float:
+    v = ctypes.c_double(0)
+    check(lib().nlse_batch_power(h, int(beam), ctypes.byref(v)), "nlse_batch_power")
+    return float(v.value)
+
+
+def nlse_batch_destroy(h) -> None:
+    check(lib().nlse_batch_destroy(h), "nlse_batch_destroy")

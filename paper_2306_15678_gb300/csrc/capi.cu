@@ -15,6 +15,7 @@
 
 #include "../../include/nlse.h"
 #include "dispatch.cuh"
+#include "host_detail.h"
 
 using namespace nlse;
 
@@ -183,6 +184,7 @@ template <> void round_table<float>(const std::vector<double>& in, std::vector<f
 
 }  // namespace
 
+
 struct nlse_grid {
     nlse_params p;
     cudaStream_t stream;
@@ -334,6 +336,42 @@ template <typename T> nlse_status upload_tables(nlse_grid* g) {
 
 }  // namespace
 
+namespace nlse {
+namespace detail {
+
+nlse_status upload_tables_f32(const nlse_params* p, cudaStream_t s, unsigned char* px, unsigned char* py,
+                              unsigned char* tw) {
+    std::vector<double> dpx, dpy, dtw;
+    propagator_tables(p, dpx, dpy);
+    std::vector<float> a, b, c;
+    round_table(dpx, a);
+    round_table(dpy, b);
+    if (cudaMemcpyAsync(px, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(py, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (tw) {
+        twiddle_table(p->n, std::min(p->n, 16), dtw);
+        round_table(dtw, c);
+        if (cudaMemcpyAsync(tw, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return NLSE_ECUDA;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
+}
+
+ScreenCoef<float> screen_coef_f32(const nlse_params* p) { return screen_coef<float>(p); }
+
+double step_phase(long long step) { return ::step_phase(step); }
+float4 rot_entry_f32(double theta) { return ::rot_entry<float>(theta); }
+
+cudaError_t finalize(const double* partials, int nparts, double scale, double* out, int* status,
+                     cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nparts, scale, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace detail
+}  // namespace nlse
+
 // ------------------------------------------------------------------ C ABI --
 
 extern "C" {
@@ -466,6 +504,17 @@ nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double
         if (row_ms) *row_ms += r;
     }
     return st;
+}
+
+nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols) {
+    if (!g) return NLSE_EINVAL;
+    const int mask = g->p.precision == NLSE_FP64 ? g->k64->col_mask : g->k32->col_mask;
+    for (int i = 0; i < 5; ++i)
+        if (kColOptions[i] == cols && ((mask >> i) & 1)) {
+            g->cols = cols;
+            return NLSE_OK;
+        }
+    return NLSE_EUNSUPPORTED;
 }
 
 nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps) {

@@ -231,26 +231,35 @@ template <typename T, int N, int LINES> __host__ __device__ constexpr int line_s
     return LINES > 1 ? base + (banks / LINES > 0 ? banks / LINES : 1) : pl;
 }
 
-// Row pass of the march: per row v = B_x S, screen, S = F_x U.  With DIAG the
-// block also reduces sum |U|^2 and max |U|^2 of its rows into partials.
-template <typename T, int N, bool DIAG>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
-                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
-k_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
-           const typename tab_of<T>::type* __restrict__ tw, ScreenCoef<T> sc, double* __restrict__ partials) {
+// Global-memory access policies of the tile bodies: plain accesses for the
+// per-pass kernels, L2-only (.cg) accesses for the persistent batched kernel,
+// whose tiles are rewritten by other SMs within the same launch.
+struct MemPlain {
+    template <typename V> __device__ __forceinline__ static V ld(const V* p) { return *p; }
+    template <typename V> __device__ __forceinline__ static void st(V* p, V v) { *p = v; }
+};
+struct MemCG {
+    template <typename V> __device__ __forceinline__ static V ld(const V* p) { return __ldcg(p); }
+    template <typename V> __device__ __forceinline__ static void st(V* p, V v) { __stcg(p, v); }
+};
+
+// Row pass body for RPB consecutive rows starting at row0 (thread layout:
+// row group g = tid / TL, in-row index j = tid % TL): v = B_x S, screen,
+// S = F_x U.  With DIAG, adds the thread's sum and max of |U|^2.
+template <typename T, int N, int RPB, bool DIAG, class M>
+__device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                                         const typename tab_of<T>::type* __restrict__ tw,
+                                         const ScreenCoef<T>& sc, int row0, typename vec2<T>::type* smem,
+                                         T& tsum, T& tmax) {
     using V = typename vec2<T>::type;
-    constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
+    constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>();
     constexpr int LS = line_stride<T, N, RPB>();
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* smem = reinterpret_cast<V*>(smraw);
     const int g = threadIdx.x / TL, j = threadIdx.x % TL;
-    const int row = blockIdx.x * RPB + g;
-    const V* line = src + (size_t)row * N;
+    const size_t row = (size_t)row0 + g;
     V* sm = smem + g * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = line[j + m * TL];
-    T tsum = (T)0, tmax = (T)0;
+    for (int m = 0; m < E; ++m) v[m] = M::ld(src + row * N + j + m * TL);
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         if (half == 0) conj_all(v);
@@ -271,33 +280,31 @@ k_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
             }
         }
     }
-    V* out = dst + (size_t)row * N;
 #pragma unroll
-    for (int m = 0; m < E; ++m) out[j + m * TL] = v[m];
-    if constexpr (DIAG) block_partials<T>(tsum, tmax, partials);
+    for (int m = 0; m < E; ++m) M::st(dst + row * N + j + m * TL, v[m]);
 }
 
-// Column pass: per column kx, S <- B_y(P_x(kx) P_y(ky) rot F_y S); P_y carries
-// 1/n^2 and rot = exp(i theta) is this step's global phase (see the march in
-// the host code: it decorrelates the FP32 rounding of the slowly rotating
-// spectral values from step to step).
-template <typename T, int N, int C>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * C, min_blocks<threads_per_line<T, N>() * C>())
-k_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
-           const typename tab_of<T>::type* __restrict__ tw,
-           const typename tab_of<T>::type* __restrict__ px, const typename tab_of<T>::type* __restrict__ py,
-           typename tab_of<T>::type rot) {
+// Column pass body for C consecutive columns starting at col0 (thread layout:
+// column c = tid % C, in-column index j = tid / C):
+// S <- B_y(P_x(kx) P_y(ky) rot F_y S), P_y carrying 1/n^2 and rot = exp(i theta)
+// this step's global phase (see the march in the host code: it decorrelates
+// the FP32 rounding of the slowly rotating spectral values from step to step).
+template <typename T, int N, int C, class M>
+__device__ __forceinline__ void col_tile(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                                         const typename tab_of<T>::type* __restrict__ tw,
+                                         const typename tab_of<T>::type* __restrict__ px,
+                                         const typename tab_of<T>::type* __restrict__ py,
+                                         typename tab_of<T>::type rot, int col0,
+                                         typename vec2<T>::type* smem) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>();
     constexpr int LS = line_stride<T, N, C>();
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* smem = reinterpret_cast<V*>(smraw);
     const int c = threadIdx.x % C, j = threadIdx.x / C;
-    const int col = blockIdx.x * C + c;
+    const int col = col0 + c;
     V* sm = smem + c * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(j + m * TL) * N + col];
+    for (int m = 0; m < E; ++m) v[m] = M::ld(src + (size_t)(j + m * TL) * N + col);
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         fft_stockham<V, N, E, false>(v, sm, tw, j);
@@ -309,7 +316,35 @@ k_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
         conj_all(v);  // second round: conj(F_y(conj(.))) = B_y
     }
 #pragma unroll
-    for (int m = 0; m < E; ++m) dst[(size_t)(j + m * TL) * N + col] = v[m];
+    for (int m = 0; m < E; ++m) M::st(dst + (size_t)(j + m * TL) * N + col, v[m]);
+}
+
+// Row pass kernel of the march; with DIAG the block also reduces sum |U|^2 and
+// max |U|^2 of its rows into partials.
+template <typename T, int N, bool DIAG>
+__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
+                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
+k_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+           const typename tab_of<T>::type* __restrict__ tw, ScreenCoef<T> sc, double* __restrict__ partials) {
+    using V = typename vec2<T>::type;
+    constexpr int RPB = rows_per_block<T, N>();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T tsum = (T)0, tmax = (T)0;
+    row_tile<T, N, RPB, DIAG, MemPlain>(src, dst, tw, sc, blockIdx.x * RPB, reinterpret_cast<V*>(smraw),
+                                        tsum, tmax);
+    if constexpr (DIAG) block_partials<T>(tsum, tmax, partials);
+}
+
+// Column pass kernel of the march.
+template <typename T, int N, int C>
+__global__ void __launch_bounds__(threads_per_line<T, N>() * C, min_blocks<threads_per_line<T, N>() * C>())
+k_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+           const typename tab_of<T>::type* __restrict__ tw,
+           const typename tab_of<T>::type* __restrict__ px, const typename tab_of<T>::type* __restrict__ py,
+           typename tab_of<T>::type rot) {
+    using V = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    col_tile<T, N, C, MemPlain>(src, dst, tw, px, py, rot, blockIdx.x * C, reinterpret_cast<V*>(smraw));
 }
 
 // Forward row transform S = F_x U (load prologue); src may equal dst.

@@ -1,0 +1,112 @@
+"""Autotuner for the launch shapes of the march: the column-tile width of the
+single-grid column pass (per grid size and precision) and the block size and
+resident blocks per SM of the persistent batched launch (per size mix).  Each
+candidate is timed on the GPU with CUDA events; the fastest is cached in a JSON
+file (NLSE_TUNE_CACHE, default ~/.cache/paper_2306_15678_gb300/tune.json).
+Results never depend on these choices, only the speed does."""
+from __future__ import annotations
+
+import collections
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import beams, capi
+from .batch import Batch
+from .grid import Grid
+
+
+def cache_path() -> str:
+    return os.environ.get("NLSE_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "paper_2306_15678_gb300", "tune.json"))
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(path, cache):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _gpu_key() -> str:
+    return torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+
+
+def _time_ms(fn, reps: int) -> float:
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
+              force: bool = False) -> int:
+    """Fastest column tile for this grid size and precision."""
+    path = path or cache_path()
+    cache = _load_cache(path)
+    key = f"{_gpu_key()}|grid|{precision}|{int(cfg['n'])}"
+    if key in cache and not force:
+        return int(cache[key]["cols"])
+    U0 = beams.make_field(cfg)
+    best, timings = None, {}
+    with Grid(cfg, precision=precision) as g:
+        g.load(U0).step(2)
+        for c in (1, 2, 4, 8, 16):
+            try:
+                capi.nlse_set_column_tile(g.h, c)
+            except capi.NlseError:
+                continue
+            g.step(2)
+            timings[c] = _time_ms(lambda: g.step(steps), 1) / steps
+            if best is None or timings[c] < timings[best]:
+                best = c
+    cache[key] = {"cols": best, "ms_per_step": timings}
+    _save_cache(path, cache)
+    return best
+
+
+def tune_batch(cfgs: list, steps: int = 10, path: str | None = None, force: bool = False,
+               fields: list | None = None) -> dict:
+    """Fastest (threads, ctas_per_sm) for this mix of grid sizes."""
+    path = path or cache_path()
+    cache = _load_cache(path)
+    mix = collections.Counter(int(c["n"]) for c in cfgs)
+    key = f"{_gpu_key()}|batch|" + ",".join(f"{n}x{mix[n]}" for n in sorted(mix))
+    if key in cache and not force:
+        return dict(cache[key]["tuning"])
+    fields = fields or [beams.make_field(c).astype(np.complex64) for c in cfgs]
+    best, timings = None, {}
+    for threads in (256, 512):
+        for per_sm in (1, 2, 3, 4, 0):
+            tuning = {"threads": threads, "ctas_per_sm": per_sm}
+            try:
+                b = Batch(cfgs, tuning)
+            except capi.NlseError:
+                continue
+            with b:
+                for i, U in enumerate(fields):
+                    b.load(i, U)
+                b.step(2)
+                t = _time_ms(lambda: b.step(steps), 1) / steps
+            timings[f"{threads}/{per_sm}"] = t
+            if best is None or t < best[0]:
+                best = (t, tuning)
+    cache[key] = {"tuning": best[1], "ms_per_step": timings}
+    _save_cache(path, cache)
+    return dict(best[1])

@@ -172,9 +172,8 @@ def test_sparse_grid_fit_full_run_is_deterministic_and_finite():
     """The whole 400-step run.  Past the first collapse the 2.5 cm march is
     chaotic (finite differences of J no longer converge as h -> 0 and FP32/FP64
     trajectories separate), so here the checks are the ones that hold at any
-    length: finite results, bit-identical gradients for different checkpoint
-    spacings, and agreement of the FP64 adjoint with central differences in the
-    well-conditioned Kerr gain."""
+    length: finite results and bit-identical gradients for different checkpoint
+    spacings."""
     cfg, U0, D = sparse_fit_case()
     a = run_gpu(cfg, U0, D, 400, 20, "fp32")
     b = run_gpu(cfg, U0, D, 400, 40, "fp32")
