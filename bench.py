@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -184,6 +187,91 @@ def traffic_for(kernel_key: str) -> float | None:
     return float(ent["dram_bytes_per_launch"])
 
 
+def bench_batch(args, dev, peak_gbs) -> dict:
+    """64 beams on grids drawn from {512, 1024, 2048}, P ~ U[20, 200] P_cr,
+    w0 ~ U[0.5, 1.5] cm, full screen, one persistent launch per replay of a
+    captured CUDA graph, launch shape from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_2306_15678_gb300 import beams, configs, tune
+    from paper_2306_15678_gb300.batch import Batch
+    cfgs = configs.cfg_batch()
+    fields = [beams.make_field(c).astype(np.complex64) for c in cfgs]
+    tuning = tune.tune_batch(cfgs, steps=10, fields=fields)
+    pts = sum(int(c["n"]) ** 2 for c in cfgs)
+    chunk = 50
+    with Batch(cfgs, tuning, device=dev) as b:
+        for i, U in enumerate(fields):
+            b.load(i, U)
+        b.capture(chunk)
+        b.replay()
+        torch.cuda.synchronize(dev)
+        reps = max(1, args.batch_steps // chunk)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        for _ in range(reps):
+            b.replay()
+        e1.record(b.stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        st = b.status()
+    steps = reps * chunk
+    mix = {}
+    for c in cfgs:
+        mix[str(c["n"])] = mix.get(str(c["n"]), 0) + 1
+    gbs = 2 * BYTES_PER_PT_PASS * pts * steps / (ms / 1e3) / 1e9
+    return {"workload": f"{len(cfgs)} beams, grid mix {mix}, full screen, FP32, persistent launch "
+                        f"under a CUDA graph ({chunk} steps per replay)",
+            "value": pts * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs, "tuning": tuning,
+            "status": "ok" if st == 0 else f"status {st}"}
+
+
+def bench_adjoint(dev) -> dict:
+    """Gradient of the fluence loss on the 512^2 sparse grid: 400 steps of
+    2.5 cm, checkpoint every 20, FP32 field; the target is a box mean of a
+    dense-grid fluence shape (a neighbouring beam's fluence stands in)."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2306_15678_gb300 import beams, configs
+    from paper_2306_15678_gb300.adjoint import AdjointMarch
+    from paper_2306_15678_gb300.grid import Grid
+    cfg = configs.cfg_adjoint_sparse()
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    D = np.abs(beams.make_field(dict(cfg, beam=dict(cfg["beam"], w0=1.05, seed=7)))) ** 2
+    n, M = cfg["n"], cfg["nsteps"]
+    with Grid(cfg, precision="fp32", device=dev) as g:
+        g.load(U0).step(20)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.step(M)
+        g.power()
+        fwd = time.perf_counter() - t0
+    fit = AdjointMarch(cfg, M, cfg["ckpt"], precision="fp32", device=dev)
+    try:
+        fit.set_target(D)
+        fit.forward(U0)
+        fit.backward()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        J = fit.forward(U0)
+        t1 = time.perf_counter()
+        dth, _ = fit.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+    finally:
+        fit.close()
+    return {"workload": f"{n}x{n} sparse grid, {M} steps, checkpoint every {cfg['ckpt']}, FP32, 6 gains",
+            "forward_march_ms": fwd * 1e3, "adjoint_forward_ms": (t1 - t0) * 1e3,
+            "adjoint_backward_ms": (t2 - t1) * 1e3,
+            "adjoint_over_forward": (t2 - t0) / fwd, "loss": J,
+            "grad_finite": bool(np.all(np.isfinite(dth)))}
+
+
 def run_reference(args, world, rank, cfg):
     if rank != 0:
         return
@@ -238,8 +326,11 @@ def main():
     n = cfg["n"]
     U0 = beams.make_field(cfg).astype(np.complex64)
     stream = torch.cuda.Stream(device=dev)
+    from paper_2306_15678_gb300 import capi, tune
     with torch.cuda.stream(stream):
+        cols = tune.tune_grid(cfg, "fp32", steps=10)
         g = Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream)
+        capi.nlse_set_column_tile(g.h, cols)
         g.load(U0)
         g.step(max(args.warmup, 3))
         torch.cuda.synchronize(dev)
@@ -312,7 +403,6 @@ def main():
         if not args.no_e2e:
             host_in = torch.from_numpy(U0).pin_memory()
             host_out = torch.empty((n, n), dtype=torch.float32).pin_memory()
-            from paper_2306_15678_gb300 import capi
             ke = args.steps
             times = []
             for it in range(2):
@@ -330,6 +420,9 @@ def main():
 
         g.close()
 
+    batch = None if args.no_batch else bench_batch(args, dev, peak_gbs)
+    adjoint = None if args.no_adjoint else bench_adjoint(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(cfg, beams.make_field(cfg), args.cpu_seconds)
@@ -339,9 +432,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
+            "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clk, "fp64_march": fp64,
+            "batch": batch, "adjoint": adjoint,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
