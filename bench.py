@@ -326,7 +326,7 @@ def main():
     n = cfg["n"]
     U0 = beams.make_field(cfg).astype(np.complex64)
     stream = torch.cuda.Stream(device=dev)
-    from paper_2306_15678_gb300 import capi, tune
+    from paper_2306_15678_gb300 import capi, shard, tune
     with torch.cuda.stream(stream):
         cols = tune.tune_grid(cfg, "fp32", steps=10)
         g = Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream)
@@ -352,11 +352,8 @@ def main():
         barrier()
         ms = e0.elapsed_time(e1)
         clk = clocks.stop()
-        if dist is not None:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * n * n * args.steps / (ms / 1e3)
+        # replicas: sum of every rank's point-steps over the slowest rank's time
+        value, ms = shard.aggregate(float(n * n * args.steps), ms, dist, dev)
 
         # ---- per-kernel times for the roofline (events around every launch)
         kroof = min(args.steps, 500)
