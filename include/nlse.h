@@ -141,9 +141,16 @@ nlse_status nlse_step(nlse_grid* g, int32_t nsteps);
  * for the per-kernel roofline; the paper has no counterpart. */
 nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double* row_ms);
 
-/* Column-tile width of the column pass (1, 2, 4, 8 or 16 columns per block;
- * NLSE_EUNSUPPORTED for a width this size cannot use).  Chosen by the
- * autotuner; results do not depend on it. */
+/* Column tile of the column pass: a width of 1, 2, 4, 8 or 16 columns per
+ * block, or'ed with NLSE_COL_TMA for the variant that moves the tile between
+ * global and shared memory with bulk tensor copies (cp.async.bulk.tensor,
+ * 256-row boxes) instead of per-thread loads and stores; that variant exists
+ * where a tile row is a multiple of 16 bytes and n a multiple of 256.
+ * NLSE_EUNSUPPORTED for a tile this size cannot use.  Chosen by the
+ * autotuner; results do not depend on it, bit for bit.  A bounded wait (1 s)
+ * of the staged variant that runs out makes the block skip its tile and sets
+ * NLSE_ETIMEOUT in the device status word (nlse_device_status). */
+enum { NLSE_COL_TMA = 0x100 };
 nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols);
 
 /* Number of z steps taken since the last load. */

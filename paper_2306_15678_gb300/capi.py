@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libnlse.so")
 
 NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
 NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
+NLSE_COL_TMA = 0x100  # column tile staged with bulk tensor copies (or'ed with the width)
 NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15
 NLSE_FP64, NLSE_FP32 = 0, 1
 

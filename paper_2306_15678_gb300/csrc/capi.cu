@@ -195,6 +195,7 @@ struct nlse_grid {
     int64_t hist_count;
     int loaded;
     int cols;  // column tile of the column pass
+    unsigned debug_extra_tx;  // test hook of the staged column pass (NLSE_DEBUG_COL_EXTRA_TX), 0 in use
     double theta;  // accumulated global phase of the stored field, mod 2 pi
     const KernelSet<float>* k32;
     const KernelSet<double>* k64;
@@ -262,7 +263,8 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const double th = step_phase(g->steps + 1);
-        cudaError_t e = ks->col_pass(field, field, tw, px, py, rot_entry<T>(th), g->cols, g->stream);
+        cudaError_t e = ks->col_pass(field, field, tw, px, py, rot_entry<T>(th), g->cols,
+                                     reinterpret_cast<int*>(g->ws + g->lay.status), g->debug_extra_tx, g->stream);
         g->theta = std::fmod(g->theta + th, kTwoPi);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 1], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -426,10 +428,11 @@ nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_works
         g->cols = g->k32->col_default;
         g->sc32 = screen_coef<float>(p);
     }
+    if (const char* env = std::getenv("NLSE_DEBUG_COL_EXTRA_TX")) g->debug_extra_tx = (unsigned)std::atoi(env);
     if (const char* env = std::getenv("NLSE_COL_TILE")) {
         const int c = std::atoi(env);
         const int mask = p->precision == NLSE_FP64 ? g->k64->col_mask : g->k32->col_mask;
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < kColOptionCount; ++i)
             if (kColOptions[i] == c && ((mask >> i) & 1)) g->cols = c;
     }
     st = p->precision == NLSE_FP64 ? upload_tables<double>(g) : upload_tables<float>(g);
@@ -509,7 +512,7 @@ nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double
 nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols) {
     if (!g) return NLSE_EINVAL;
     const int mask = g->p.precision == NLSE_FP64 ? g->k64->col_mask : g->k32->col_mask;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < kColOptionCount; ++i)
         if (kColOptions[i] == cols && ((mask >> i) & 1)) {
             g->cols = cols;
             return NLSE_OK;
@@ -769,7 +772,7 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
                             cudaMemcpyDeviceToDevice, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
         if (ks->col_pass(state, state, tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
-                         rot_entry<T>(step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+                         rot_entry<T>(step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
         if (ks->row_pass(state, state, tw, sc, partials, false, a->stream) != cudaSuccess) return NLSE_ECUDA;
     }
@@ -807,7 +810,7 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
             return NLSE_ECUDA;
         for (int s = c0; s < c1; ++s) {  // recompute the segment, keeping T_s
             if (ks->col_pass(state, seg(s - c0), tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
-                             rot_entry<T>(step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+                             rot_entry<T>(step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             if (s + 1 < c1 &&
                 ks->row_pass(seg(s - c0), state, tw, ac.sc, partials, false, a->stream) != cudaSuccess)
@@ -816,7 +819,7 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
         for (int s = c1 - 1; s >= c0; --s) {  // reverse the segment
             if (ks->adj_row(gam, seg(s - c0), tw, ac, acc, a->stream) != cudaSuccess) return NLSE_ECUDA;
             if (ks->col_pass(gam, gam, tw, atab<T>(a, a->lay.pxc), atab<T>(a, a->lay.pyc),
-                             rot_entry<T>(-step_phase(s + 1)), a->cols, a->stream) != cudaSuccess)
+                             rot_entry<T>(-step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
         }
     }

@@ -3,13 +3,21 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include "adjoint.cuh"
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace nlse {
 
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per block (sm_100/103)
-constexpr int kColOptions[5] = {1, 2, 4, 8, 16};
+// column-tile codes: a width of 1..16 columns per block, or'ed with kColTma
+// for the variant that stages the tile with bulk tensor copies (tma.cuh)
+constexpr int kColTma = 0x100;
+constexpr int kColOptionCount = 10;
+constexpr int kColOptions[kColOptionCount] = {1, 2, 4, 8, 16,
+                                              kColTma | 1, kColTma | 2, kColTma | 4, kColTma | 8, kColTma | 16};
 
 template <typename T> struct KernelSet {
     using V = typename vec2<T>::type;
@@ -20,8 +28,10 @@ template <typename T> struct KernelSet {
     int col_default;   // default column tile
     cudaError_t (*row_pass)(const V* src, V* dst, const W* tw, ScreenCoef<T> sc, double* partials,
                             bool diag, cudaStream_t s);
+    // status: device status word (bit 1: a bounded wait ran out), may be null;
+    // extra_tx: test hook of the staged variant (0 in use)
     cudaError_t (*col_pass)(const V* src, V* dst, const W* tw, const W* px, const W* py, W rot,
-                            int cols, cudaStream_t s);
+                            int cols, int* status, unsigned extra_tx, cudaStream_t s);
     cudaError_t (*row_forward)(const V* src, V* dst, const W* tw, cudaStream_t s);
     cudaError_t (*readout)(const V* state, const W* tw, V* field_out, T* flu_out, double* partials,
                            V unrot, cudaStream_t s);
@@ -89,17 +99,73 @@ cudaError_t launch_col_c(const typename vec2<T>::type* src, typename vec2<T>::ty
     }
 }
 
+// Tensor map of an n x n complex field as n rows of 2n words (4-byte words
+// for complex64, 8-byte for complex128: the copies move bits, no conversion),
+// boxes of 2C words x 256 rows.  cuTensorMapEncodeTiled is a host-only driver
+// call, reached through the runtime's entry-point query so that the library
+// needs no link to libcuda.
+inline cudaError_t encode_field_map(CUtensorMap* map, const void* base, int n, int word_bytes, int cols) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * n * word_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * cols), (cuuint32_t)kTmaBoxRows};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = fn(map, word_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+                          const_cast<void*>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T, int N, int C>
+cudaError_t launch_col_tma_c(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+                             const typename tab_of<T>::type* tw,
+                             const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
+                             typename tab_of<T>::type rot, int* status, unsigned extra_tx, cudaStream_t s) {
+    if constexpr (col_valid<T, N, C>() && col_tma_valid<T, N, C>()) {
+        constexpr int SMEM = col_smem_bytes<T, N, C>() + kTmaAlignPad;
+        CUtensorMap ml, ms;
+        cudaError_t e = encode_field_map(&ml, src, N, (int)sizeof(T), C);
+        if (e == cudaSuccess) {
+            if (static_cast<const void*>(src) == static_cast<const void*>(dst)) ms = ml;
+            else e = encode_field_map(&ms, dst, N, (int)sizeof(T), C);
+        }
+        if (e == cudaSuccess) e = ensure_smem<k_col_pass_tma<T, N, C>>(SMEM);
+        if (e != cudaSuccess) return e;
+        k_col_pass_tma<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(ml, ms, tw, px, py, rot, status,
+                                                                                  extra_tx);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidConfiguration;
+    }
+}
+
 template <typename T, int N>
 cudaError_t launch_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
                             const typename tab_of<T>::type* tw,
                             const typename tab_of<T>::type* px, const typename tab_of<T>::type* py,
-                            typename tab_of<T>::type rot, int cols, cudaStream_t s) {
+                            typename tab_of<T>::type rot, int cols, int* status, unsigned extra_tx,
+                            cudaStream_t s) {
     switch (cols) {
         case 1: return launch_col_c<T, N, 1>(src, dst, tw, px, py, rot, s);
         case 2: return launch_col_c<T, N, 2>(src, dst, tw, px, py, rot, s);
         case 4: return launch_col_c<T, N, 4>(src, dst, tw, px, py, rot, s);
         case 8: return launch_col_c<T, N, 8>(src, dst, tw, px, py, rot, s);
         case 16: return launch_col_c<T, N, 16>(src, dst, tw, px, py, rot, s);
+        case kColTma | 1: return launch_col_tma_c<T, N, 1>(src, dst, tw, px, py, rot, status, extra_tx, s);
+        case kColTma | 2: return launch_col_tma_c<T, N, 2>(src, dst, tw, px, py, rot, status, extra_tx, s);
+        case kColTma | 4: return launch_col_tma_c<T, N, 4>(src, dst, tw, px, py, rot, status, extra_tx, s);
+        case kColTma | 8: return launch_col_tma_c<T, N, 8>(src, dst, tw, px, py, rot, status, extra_tx, s);
+        case kColTma | 16: return launch_col_tma_c<T, N, 16>(src, dst, tw, px, py, rot, status, extra_tx, s);
         default: return cudaErrorInvalidConfiguration;
     }
 }
@@ -150,10 +216,15 @@ cudaError_t launch_adj_row(typename vec2<T>::type* gam, const typename vec2<T>::
     return cudaGetLastError();
 }
 
+template <typename T, int N, int C> constexpr bool col_tma_ok() {
+    return col_valid<T, N, C>() && col_tma_valid<T, N, C>();
+}
 template <typename T, int N> constexpr int col_mask() {
     return (col_valid<T, N, 1>() ? 1 : 0) | (col_valid<T, N, 2>() ? 2 : 0) |
            (col_valid<T, N, 4>() ? 4 : 0) | (col_valid<T, N, 8>() ? 8 : 0) |
-           (col_valid<T, N, 16>() ? 16 : 0);
+           (col_valid<T, N, 16>() ? 16 : 0) | (col_tma_ok<T, N, 1>() ? 32 : 0) |
+           (col_tma_ok<T, N, 2>() ? 64 : 0) | (col_tma_ok<T, N, 4>() ? 128 : 0) |
+           (col_tma_ok<T, N, 8>() ? 256 : 0) | (col_tma_ok<T, N, 16>() ? 512 : 0);
 }
 
 // default column tile: the widest valid tile of at most 512 threads, unless

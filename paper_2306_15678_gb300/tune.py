@@ -55,9 +55,13 @@ def _time_ms(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+TILE_CODES = tuple(w | t for t in (0, capi.NLSE_COL_TMA) for w in (1, 2, 4, 8, 16))
+
+
 def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
               force: bool = False) -> int:
-    """Fastest column tile for this grid size and precision."""
+    """Fastest column-tile code (a width, or'ed with NLSE_COL_TMA for the
+    variant staged by bulk tensor copies) for this grid size and precision."""
     path = path or cache_path()
     cache = _load_cache(path)
     key = f"{_gpu_key()}|grid|{precision}|{int(cfg['n'])}"
@@ -67,7 +71,7 @@ def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | N
     best, timings = None, {}
     with Grid(cfg, precision=precision) as g:
         g.load(U0).step(2)
-        for c in (1, 2, 4, 8, 16):
+        for c in TILE_CODES:
             try:
                 capi.nlse_set_column_tile(g.h, c)
             except capi.NlseError:

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2306_15678_gb300 import beams, capi, configs
+from paper_2306_15678_gb300 import beams, capi, configs, tune
 from paper_2306_15678_gb300.grid import Grid
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +56,54 @@ def test_every_column_tile_agrees(prec, n, monkeypatch):
             outs.append(g.load(U0).step(3).field())
     for U in outs:
         assert rel_l2(U, ref) < (1e-11 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec,n", [("fp32", 4096), ("fp32", 2048), ("fp32", 512), ("fp64", 1024)])
+def test_column_tiles_bit_identical(prec, n):
+    """The column tile (its width, and per-thread accesses or bulk tensor
+    copies) changes which threads transform which column and how the tile
+    reaches shared memory, not the arithmetic: every valid tile gives the
+    same bits, and the staged variant exists at these sizes."""
+    cfg = configs.scaled(configs.cfg_dense_fp32(), n, nsteps=2)
+    U0 = beams.make_field(cfg)
+    if prec == "fp32":
+        U0 = U0.astype(np.complex64)
+    outs = {}
+    with Grid(cfg, precision=prec) as g:
+        for c in tune.TILE_CODES:
+            try:
+                capi.nlse_set_column_tile(g.h, c)
+            except capi.NlseError as e:
+                assert e.status == capi.NLSE_EUNSUPPORTED
+                continue
+            outs[c] = g.load(U0).step(3).field()
+        assert g.device_status() == capi.NLSE_OK
+    assert any(c & capi.NLSE_COL_TMA for c in outs)
+    ref = next(iter(outs.values()))
+    for c, U in outs.items():
+        assert np.array_equal(U, ref), hex(c)
+
+
+def test_staged_column_pass_wait_runs_out_cleanly(monkeypatch):
+    """Block 0 of the staged column pass is made to expect 16 bytes that its
+    copies never bring: its bounded wait runs out after 1 s, the grid reports
+    NLSE_ETIMEOUT, and the context stays usable for the next grid."""
+    cfg = beam_cfg(512, configs.ALL_TERMS, dz=2.0, L=0.64, w0=0.05)
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    monkeypatch.setenv("NLSE_DEBUG_COL_EXTRA_TX", "16")
+    with Grid(cfg, precision="fp32") as g:
+        capi.nlse_set_column_tile(g.h, 4 | capi.NLSE_COL_TMA)
+        g.load(U0).step(1)
+        torch.cuda.synchronize()
+        assert g.device_status() == capi.NLSE_ETIMEOUT
+        assert g.device_status() == capi.NLSE_OK  # reading clears the word
+    monkeypatch.delenv("NLSE_DEBUG_COL_EXTRA_TX")
+    ref, _, _ = oracle.march(U0.astype(np.complex128), cfg, 3)
+    with Grid(cfg, precision="fp32") as g:
+        capi.nlse_set_column_tile(g.h, 4 | capi.NLSE_COL_TMA)
+        U = g.load(U0).step(3).field()
+        assert g.device_status() == capi.NLSE_OK
+    assert rel_l2(U, ref) < 1e-5
 
 
 # ------------------------------------------------------------ plain FP64
