@@ -36,9 +36,9 @@ constexpr int kRotSteps = 1 << 20;  // steps covered by the per-step phase table
 
 struct BatchBeam {
     float2* field;
-    const float4* px;
-    const float4* py;
-    const float4* tw;
+    const float2* px;  // kDither copies of n entries each (copy k mod kDither serves step k)
+    const float2* py;
+    const float2* tw;
     ScreenCoef<float> sc;
     int log2n;
     int col_tiles;
@@ -59,7 +59,7 @@ struct BatchPlan {
     int* status;
     int* abort;
     const long long* step_base;  // steps taken before this launch
-    const float4* rot;           // rot[s] = exp(i theta_{s+1}) as an FP32 hi/lo pair
+    const float2* rot;           // rot[k] = exp(i theta_{k+1}) in FP32 (k: 0-based global step)
     long long timeout_ns;
     long long skip_item;  // test hook: this item never reports completion (-1: none)
 };
@@ -89,15 +89,19 @@ template <int THREADS> constexpr int batch_smem_max() {
                      batch_smem<THREADS, 2048>(), batch_smem<THREADS, 4096>()});
 }
 
+// one tile of global step k with the step's table copy, as a single grid applies it
 template <int THREADS, int N>
-__device__ __forceinline__ void batch_tile(const BatchBeam& bm, bool col, int tile, float4 rot, float2* smem) {
+__device__ __forceinline__ void batch_tile(const BatchBeam& bm, bool col, int tile, long long k, float2 rot,
+                                           float2* smem) {
     if constexpr (batch_supported<THREADS, N>()) {
         constexpr int L = tile_lines<THREADS, N>();
+        const size_t copy = (size_t)(k & (kDither - 1)) * N;
+        const float2* tw = bm.tw + copy;
         if (col) {
-            col_tile<float, N, L, MemCG>(bm.field, bm.field, bm.tw, bm.px, bm.py, rot, tile * L, smem);
+            col_tile<float, N, L, MemCG>(bm.field, bm.field, tw, bm.px + copy, bm.py + copy, rot, tile * L, smem);
         } else {
             float ts = 0.f, tm = 0.f;
-            row_tile<float, N, L, false, MemCG>(bm.field, bm.field, bm.tw, bm.sc, tile * L, smem, ts, tm);
+            row_tile<float, N, L, false, MemCG>(bm.field, bm.field, tw, bm.sc, tile * L, smem, ts, tm);
         }
     }
 }
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(THREADS, min_blocks<THREADS>()) k_batch_march(
     extern __shared__ __align__(16) unsigned char smraw[];
     float2* smem = reinterpret_cast<float2*>(smraw);
     __shared__ int s_item_step, s_item_beam, s_item_tile, s_item_col, s_stop;
-    __shared__ float4 s_rot;
+    __shared__ float2 s_rot;
+    __shared__ long long s_k;
     const long long total = (long long)plan.items_per_step * plan.nsteps;
     const int col_total = plan.col_off[plan.nbeams];
     for (;;) {
@@ -145,7 +150,9 @@ __global__ void __launch_bounds__(THREADS, min_blocks<THREADS>()) k_batch_march(
                         __nanosleep(100);
                     }
                 }
-                if (col) s_rot = plan.rot[*plan.step_base + s];  // this step's global phase
+                const long long k = *plan.step_base + s;  // global step index
+                s_k = k;
+                s_rot = plan.rot[k];  // this step's global phase
                 s_item_step = (int)(i & 0x7fffffff);
                 s_item_beam = lo;
                 s_item_tile = rr - off[lo];
@@ -158,14 +165,15 @@ __global__ void __launch_bounds__(THREADS, min_blocks<THREADS>()) k_batch_march(
         const int b = s_item_beam, tile = s_item_tile;
         const bool col = s_item_col != 0;
         const long long item = s_item_step;
-        const float4 rot = s_rot;
+        const float2 rot = s_rot;
+        const long long k = s_k;
         const BatchBeam bm = plan.beams[b];
         switch (bm.log2n) {
-            case 8: batch_tile<THREADS, 256>(bm, col, tile, rot, smem); break;
-            case 9: batch_tile<THREADS, 512>(bm, col, tile, rot, smem); break;
-            case 10: batch_tile<THREADS, 1024>(bm, col, tile, rot, smem); break;
-            case 11: batch_tile<THREADS, 2048>(bm, col, tile, rot, smem); break;
-            case 12: batch_tile<THREADS, 4096>(bm, col, tile, rot, smem); break;
+            case 8: batch_tile<THREADS, 256>(bm, col, tile, k, rot, smem); break;
+            case 9: batch_tile<THREADS, 512>(bm, col, tile, k, rot, smem); break;
+            case 10: batch_tile<THREADS, 1024>(bm, col, tile, k, rot, smem); break;
+            case 11: batch_tile<THREADS, 2048>(bm, col, tile, k, rot, smem); break;
+            case 12: batch_tile<THREADS, 4096>(bm, col, tile, k, rot, smem); break;
             default: break;
         }
         __threadfence();  // this thread's tile stores, before the completion signal
@@ -225,8 +233,8 @@ BLayout blayout(int count, const nlse_params* ps) {
         L.field[b] = o; o = al256(o + (size_t)ps[b].n * ps[b].n * 8);
     }
     for (int b = 0; b < count; ++b) {
-        L.px[b] = o; o = al256(o + (size_t)ps[b].n * 16);
-        L.py[b] = o; o = al256(o + (size_t)ps[b].n * 16);
+        L.px[b] = o; o = al256(o + (size_t)kDither * ps[b].n * 8);
+        L.py[b] = o; o = al256(o + (size_t)kDither * ps[b].n * 8);
     }
     int maxn = 0;
     for (int k = 0; k <= kBatchMaxLog2; ++k) L.tw[k] = 0;
@@ -234,14 +242,14 @@ BLayout blayout(int count, const nlse_params* ps) {
     for (int k = kBatchMinLog2; k <= kBatchMaxLog2; ++k) {
         bool used = false;
         for (int b = 0; b < count; ++b) used |= ps[b].n == (1 << k);
-        if (used) { L.tw[k] = o; o = al256(o + ((size_t)16 << k)); }
+        if (used) { L.tw[k] = o; o = al256(o + ((size_t)kDither * 8 << k)); }
     }
     L.beams = o;     o = al256(o + sizeof(BatchBeam) * count);
     L.col_off = o;   o = al256(o + sizeof(int) * (count + 1));
     L.row_off = o;   o = al256(o + sizeof(int) * (count + 1));
     L.counters = o;  o = al256(o + sizeof(unsigned int) * (2 * count + 1) + 2 * sizeof(int));
     L.step_base = o; o = al256(o + sizeof(long long));
-    L.rot = o;       o = al256(o + sizeof(float4) * (size_t)kRotSteps);
+    L.rot = o;       o = al256(o + sizeof(float2) * (size_t)kRotSteps);
     L.partials = o;  o = al256(o + (size_t)maxn * 2 * sizeof(double));
     L.readout = o;   o = al256(o + 4 * sizeof(double) + sizeof(int));
     L.scratch = o;   o = al256(o + (size_t)maxn * maxn * 8);  // field staging for host readouts
@@ -313,7 +321,7 @@ template <int THREADS> nlse_status launch_batch(nlse_batch* B, int nsteps) {
     plan.status = reinterpret_cast<int*>(ctr + 1 + 2 * B->count);
     plan.abort = plan.status + 1;
     plan.step_base = reinterpret_cast<const long long*>(ws + B->lay.step_base);
-    plan.rot = reinterpret_cast<const float4*>(ws + B->lay.rot);
+    plan.rot = reinterpret_cast<const float2*>(ws + B->lay.rot);
     plan.timeout_ns = (long long)B->tune.timeout_ms * 1000000LL;
     plan.skip_item = B->tune.debug_skip_item;
     // reset the work counter, the completion counters and the abort flag (not the status word)
@@ -331,8 +339,11 @@ nlse_status launch_any(nlse_batch* B, int nsteps) {
 }
 
 void advance_host(nlse_batch* B, int nsteps) {
-    for (int s = 0; s < nsteps; ++s)
-        B->theta = std::fmod(B->theta + detail::step_phase(B->steps + s + 1), 6.283185307179586476925286766559);
+    for (int s = 0; s < nsteps; ++s) {
+        double th = 0.0;  // the angle step B->steps + s turns the fields by
+        detail::rot_step_f32(B->steps + s, &th);
+        B->theta = std::fmod(B->theta + th, 6.283185307179586476925286766559);
+    }
     B->steps += nsteps;
 }
 
@@ -405,9 +416,9 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
         if (st != NLSE_OK) { delete B; return st; }
         BatchBeam& d = desc[b];
         d.field = reinterpret_cast<float2*>(B->ws + lay.field[b]);
-        d.px = reinterpret_cast<const float4*>(B->ws + lay.px[b]);
-        d.py = reinterpret_cast<const float4*>(B->ws + lay.py[b]);
-        d.tw = reinterpret_cast<const float4*>(B->ws + lay.tw[B->log2n[b]]);
+        d.px = reinterpret_cast<const float2*>(B->ws + lay.px[b]);
+        d.py = reinterpret_cast<const float2*>(B->ws + lay.py[b]);
+        d.tw = reinterpret_cast<const float2*>(B->ws + lay.tw[B->log2n[b]]);
         d.sc = detail::screen_coef_f32(&params[b]);
         d.log2n = B->log2n[b];
         d.col_tiles = B->col_tiles[b];
@@ -417,9 +428,9 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
         roff[b + 1] = roff[b] + d.row_tiles;
     }
     const long long zero = 0;
-    std::vector<float4> rot(kRotSteps);
-    for (int s = 0; s < kRotSteps; ++s) rot[s] = detail::rot_entry_f32(detail::step_phase(s + 1));
-    if (cudaMemcpyAsync(B->ws + lay.rot, rot.data(), sizeof(float4) * rot.size(), cudaMemcpyHostToDevice,
+    std::vector<float2> rot(kRotSteps);
+    for (int s = 0; s < kRotSteps; ++s) rot[s] = detail::rot_step_f32(s, nullptr);
+    if (cudaMemcpyAsync(B->ws + lay.rot, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice,
                         B->stream) != cudaSuccess ||
         cudaMemcpyAsync(B->ws + lay.beams, desc.data(), sizeof(BatchBeam) * count, cudaMemcpyHostToDevice,
                         B->stream) != cudaSuccess ||
@@ -439,12 +450,23 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     return NLSE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// twiddles of the one-off transforms of a beam (load prologue, readouts): copy 0, as a single grid uses
+const float2* fixed_twiddles(const nlse_batch* B, int beam) {
+    return reinterpret_cast<const float2*>(B->ws + B->lay.tw[B->log2n[beam]]);
+}
+}  // namespace
+
+extern "C" {
+
 nlse_status nlse_batch_load_field(nlse_batch* B, int32_t beam, const void* src, int src_on_device) {
     if (!B || !src || beam < 0 || beam >= B->count) return NLSE_EINVAL;
     if (B->steps != 0) return NLSE_ESTATE;  // all beams start from the same step
     const int n = B->ps[beam].n;
     float2* f = reinterpret_cast<float2*>(B->ws + B->lay.field[beam]);
-    const float4* tw = reinterpret_cast<const float4*>(B->ws + B->lay.tw[B->log2n[beam]]);
+    const float2* tw = fixed_twiddles(B, beam);
     const KernelSet<float>* ks = kernels_f32(B->log2n[beam]);
     cudaError_t e;
     if (src_on_device) {
@@ -529,7 +551,7 @@ nlse_status nlse_batch_read_field(nlse_batch* B, int32_t beam, void* dst, int ds
     const int n = B->ps[beam].n;
     const KernelSet<float>* ks = kernels_f32(B->log2n[beam]);
     float2* f = reinterpret_cast<float2*>(B->ws + B->lay.field[beam]);
-    const float4* tw = reinterpret_cast<const float4*>(B->ws + B->lay.tw[B->log2n[beam]]);
+    const float2* tw = fixed_twiddles(B, beam);
     double* partials = reinterpret_cast<double*>(B->ws + B->lay.partials);
     float2 unrot = make_float2((float)std::cos(B->theta), (float)(-std::sin(B->theta)));
     if (dst_on_device) {
@@ -548,7 +570,7 @@ nlse_status nlse_batch_power(nlse_batch* B, int32_t beam, double* watts) {
     if (!B || !watts || beam < 0 || beam >= B->count) return NLSE_EINVAL;
     const KernelSet<float>* ks = kernels_f32(B->log2n[beam]);
     float2* f = reinterpret_cast<float2*>(B->ws + B->lay.field[beam]);
-    const float4* tw = reinterpret_cast<const float4*>(B->ws + B->lay.tw[B->log2n[beam]]);
+    const float2* tw = fixed_twiddles(B, beam);
     double* partials = reinterpret_cast<double*>(B->ws + B->lay.partials);
     double* out = reinterpret_cast<double*>(B->ws + B->lay.readout);
     if (ks->readout(f, tw, nullptr, nullptr, partials, make_float2(1.f, 0.f), B->stream) != cudaSuccess)

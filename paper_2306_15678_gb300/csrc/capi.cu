@@ -27,6 +27,12 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// bytes of one device table of n complex entries: FP32 tables hold kDither
+// dithered copies of 8-byte entries, FP64 tables one copy of 16-byte entries
+size_t table_bytes(int n, int precision) {
+    return precision == NLSE_FP64 ? (size_t)n * 16 : (size_t)kDither * n * 8;
+}
+
 int log2_exact(int n) {
     if (n <= 0 || (n & (n - 1))) return -1;
     int k = 0;
@@ -45,10 +51,10 @@ Layout layout_for(int n, int precision) {
     size_t o = 0;
     L.state = o;    o = align256(o + nn * cs);
     L.aux = o;      o = align256(o + nn * cs);
-    // table entries are 16 bytes in both precisions (FP32: hi/lo pairs)
-    L.tw = o;       o = align256(o + (size_t)n * 16);
-    L.px = o;       o = align256(o + (size_t)n * 16);
-    L.py = o;       o = align256(o + (size_t)n * 16);
+    const size_t tb = table_bytes(n, precision);
+    L.tw = o;       o = align256(o + tb);
+    L.px = o;       o = align256(o + tb);
+    L.py = o;       o = align256(o + tb);
     L.partials = o; o = align256(o + (size_t)n * 2 * sizeof(double));
     L.hist = o;     o = align256(o + (size_t)kHistCap * 2 * sizeof(double));
     L.readout = o;  o = align256(o + 2 * sizeof(double));
@@ -164,22 +170,62 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     return c;
 }
 
-// FP64 complex table -> device entries: FP32 hi/lo pairs (re_hi, im_hi, re_lo, im_lo)
-// so that each factor is exact to O(eps^2), or the FP64 values themselves
-template <typename T> void round_table(const std::vector<double>& in, std::vector<T>& out);
-template <> void round_table<double>(const std::vector<double>& in, std::vector<double>& out) {
+// Dithered rounding (see fft.cuh): the FP32 neighbour of w below or above it,
+// the one above when the fraction of an FP32 unit by which w exceeds the
+// lower neighbour is greater than the threshold u in (0, 1).
+float dround(double w, double u) {
+    float lo = (float)w;
+    if ((double)lo > w) lo = std::nextafter(lo, -INFINITY);
+    if ((double)lo == w) return lo;
+    const float hi = std::nextafter(lo, INFINITY);
+    const double frac = (w - (double)lo) / ((double)hi - (double)lo);
+    return frac > u ? hi : lo;
+}
+// fixed pseudo-random offset in [0, kDither) of (table, entry, component)
+int dither_offset(uint64_t table_id, uint64_t entry, int comp) {
+    uint64_t z = table_id * 0x9E3779B97F4A7C15ull + entry * 2 + (uint64_t)comp + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (int)(z % (uint64_t)kDither);
+}
+// identifiers of the dithered tables (distinct offsets per table)
+enum : uint64_t { kTabTwiddle = 1, kTabPx = 2, kTabPy = 3 };
+
+// FP64 complex table (re, im pairs) -> device entries: the FP64 values, or
+// kDither FP32 copies, copy d rounding entry e's component c with threshold
+// ((d + o) mod kDither + 1/2) / kDither, o = dither_offset(table, e, c)
+template <typename T> void round_table(const std::vector<double>& in, uint64_t table_id, std::vector<T>& out);
+template <>
+void round_table<double>(const std::vector<double>& in, uint64_t, std::vector<double>& out) {
     out = in;
 }
-template <> void round_table<float>(const std::vector<double>& in, std::vector<float>& out) {
+template <>
+void round_table<float>(const std::vector<double>& in, uint64_t table_id, std::vector<float>& out) {
     const size_t n = in.size() / 2;
-    out.resize(4 * n);
-    for (size_t i = 0; i < n; ++i) {
-        const float hr = (float)in[2 * i], hi = (float)in[2 * i + 1];
-        out[4 * i] = hr;
-        out[4 * i + 1] = hi;
-        out[4 * i + 2] = (float)(in[2 * i] - (double)hr);
-        out[4 * i + 3] = (float)(in[2 * i + 1] - (double)hi);
-    }
+    out.resize((size_t)kDither * 2 * n);
+    for (size_t e = 0; e < n; ++e)
+        for (int c = 0; c < 2; ++c) {
+            const int o = dither_offset(table_id, e, c);
+            for (int d = 0; d < kDither; ++d)
+                out[(size_t)d * 2 * n + 2 * e + c] = dround(in[2 * e + c], ((d + o) % kDither + 0.5) / kDither);
+        }
+}
+
+// Twiddle table of step k (0-based count of the steps taken before it): copy
+// k mod kDither in FP32, the table itself in FP64.
+template <typename T> const typename tab_of<T>::type* twiddles_at(const unsigned char* table, int n, int64_t k) {
+    const auto* t = reinterpret_cast<const typename tab_of<T>::type*>(table);
+    return sizeof(T) == 4 ? t + (size_t)(k & (kDither - 1)) * n : t;
+}
+// twiddles of the one-off transforms (load prologue, readouts): copy 0
+template <typename T> const typename tab_of<T>::type* twiddles_fixed(const unsigned char* table) {
+    return reinterpret_cast<const typename tab_of<T>::type*>(table);
+}
+// copy of a propagator table for step k
+template <typename T> const typename tab_of<T>::type* table_at(const unsigned char* table, int n, int64_t k) {
+    const auto* t = reinterpret_cast<const typename tab_of<T>::type*>(table);
+    return sizeof(T) == 4 ? t + (size_t)(k & (kDither - 1)) * n : t;
 }
 
 }  // namespace
@@ -235,14 +281,43 @@ template <typename T> VT<T>* at(nlse_grid* g, size_t off) { return reinterpret_c
 double step_phase(int64_t step) {
     return kTwoPi * std::fmod((double)step * 0.61803398874989484820, 1.0);
 }
-template <typename T> WT<T> rot_entry(double theta);
-template <> WT<float> rot_entry<float>(double theta) {
-    const double c = std::cos(theta), s = std::sin(theta);
-    const float ch = (float)c, sh = (float)s;
-    return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+// Rotation factor of step k (0-based): exp(i theta_{k+1}) as the kernels
+// apply it, and in *applied the angle it turns the field by.  In FP32 the
+// factor is, among the FP32 pairs within 4 units of (cos, sin), the one whose
+// squared modulus is closest to 1: a rounded factor would scale the power by
+// 1 + O(2^-24) every step, a random walk over thousands of steps; the angle
+// it applies instead is exact in FP64 and accumulated by the host.
+template <typename T> WT<T> rot_for_step(int64_t k, double* applied);
+template <> WT<double> rot_for_step<double>(int64_t k, double* applied) {
+    const double th = step_phase(k + 1);
+    if (applied) *applied = th;
+    return make_double2(std::cos(th), std::sin(th));
 }
-template <> WT<double> rot_entry<double>(double theta) {
-    return make_double2(std::cos(theta), std::sin(theta));
+template <> WT<float> rot_for_step<float>(int64_t k, double* applied) {
+    const double th = step_phase(k + 1);
+    const double c = std::cos(th), s = std::sin(th);
+    float cs[9], ss[9];
+    cs[4] = (float)c;
+    ss[4] = (float)s;
+    for (int i = 1; i <= 4; ++i) {
+        cs[4 + i] = std::nextafter(cs[3 + i], INFINITY);
+        cs[4 - i] = std::nextafter(cs[5 - i], -INFINITY);
+        ss[4 + i] = std::nextafter(ss[3 + i], INFINITY);
+        ss[4 - i] = std::nextafter(ss[5 - i], -INFINITY);
+    }
+    float bc = cs[4], bs = ss[4];
+    double be = std::fabs((double)bc * bc + (double)bs * bs - 1.0);
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            const double e = std::fabs((double)cs[i] * cs[i] + (double)ss[j] * ss[j] - 1.0);
+            if (e < be) { be = e; bc = cs[i]; bs = ss[j]; }
+        }
+    if (applied) *applied = std::atan2((double)bs, (double)bc);
+    return make_float2(bc, bs);
+}
+template <typename V> V conj_of(V v) {
+    v.y = -v.y;
+    return v;
 }
 template <typename T> VT<T> unrot_value(double theta) {
     VT<T> v;
@@ -255,15 +330,18 @@ inline double* dat(nlse_grid* g, size_t off) { return reinterpret_cast<double*>(
 template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_t* ev = nullptr) {
     const KernelSet<T>* ks = Sel<T>::ks(g);
     VT<T>* field = at<T>(g, g->lay.state);
-    const WT<T>* tw = tab<T>(g, g->lay.tw);
-    const WT<T>* px = tab<T>(g, g->lay.px);
-    const WT<T>* py = tab<T>(g, g->lay.py);
+    const int n = g->p.n;
     double* partials = dat(g, g->lay.partials);
     const double dx = g->p.L / g->p.n;
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
-        const double th = step_phase(g->steps + 1);
-        cudaError_t e = ks->col_pass(field, field, tw, px, py, rot_entry<T>(th), g->cols,
+        const int64_t k = g->steps;
+        const WT<T>* tw = twiddles_at<T>(g->ws + g->lay.tw, n, k);
+        const WT<T>* px = table_at<T>(g->ws + g->lay.px, n, k);
+        const WT<T>* py = table_at<T>(g->ws + g->lay.py, n, k);
+        double th = 0.0;
+        const WT<T> rot = rot_for_step<T>(k, &th);
+        cudaError_t e = ks->col_pass(field, field, tw, px, py, rot, g->cols,
                                      reinterpret_cast<int*>(g->ws + g->lay.status), g->debug_extra_tx, g->stream);
         g->theta = std::fmod(g->theta + th, kTwoPi);
         if (e != cudaSuccess) return NLSE_ECUDA;
@@ -289,7 +367,7 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
 template <typename T> nlse_status readout_impl(nlse_grid* g, VT<T>* field_out, T* flu_out) {
     const KernelSet<T>* ks = Sel<T>::ks(g);
     double* partials = dat(g, g->lay.partials);
-    cudaError_t e = ks->readout(at<T>(g, g->lay.state), tab<T>(g, g->lay.tw), field_out, flu_out,
+    cudaError_t e = ks->readout(at<T>(g, g->lay.state), twiddles_fixed<T>(g->ws + g->lay.tw), field_out, flu_out,
                                 partials, unrot_value<T>(g->theta), g->stream);
     if (e != cudaSuccess) return NLSE_ECUDA;
     const double dx = g->p.L / g->p.n;
@@ -320,9 +398,9 @@ template <typename T> nlse_status upload_tables(nlse_grid* g) {
     const int ept = std::min(g->p.n, sizeof(T) == 4 ? 16 : 8);
     twiddle_table(g->p.n, ept, tw);
     std::vector<T> a, b, c;
-    round_table(px, a);
-    round_table(py, b);
-    round_table(tw, c);
+    round_table(px, kTabPx, a);
+    round_table(py, kTabPy, b);
+    round_table(tw, kTabTwiddle, c);
     const size_t bytes = a.size() * sizeof(T);
     const size_t tw_bytes = c.size() * sizeof(T);
     cudaError_t e;
@@ -346,14 +424,14 @@ nlse_status upload_tables_f32(const nlse_params* p, cudaStream_t s, unsigned cha
     std::vector<double> dpx, dpy, dtw;
     propagator_tables(p, dpx, dpy);
     std::vector<float> a, b, c;
-    round_table(dpx, a);
-    round_table(dpy, b);
+    round_table(dpx, kTabPx, a);
+    round_table(dpy, kTabPy, b);
     if (cudaMemcpyAsync(px, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(py, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return NLSE_ECUDA;
     if (tw) {
         twiddle_table(p->n, std::min(p->n, 16), dtw);
-        round_table(dtw, c);
+        round_table(dtw, kTabTwiddle, c);
         if (cudaMemcpyAsync(tw, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return NLSE_ECUDA;
     }
@@ -362,8 +440,8 @@ nlse_status upload_tables_f32(const nlse_params* p, cudaStream_t s, unsigned cha
 
 ScreenCoef<float> screen_coef_f32(const nlse_params* p) { return screen_coef<float>(p); }
 
-double step_phase(long long step) { return ::step_phase(step); }
-float4 rot_entry_f32(double theta) { return ::rot_entry<float>(theta); }
+float2 rot_step_f32(long long k, double* applied) { return ::rot_for_step<float>(k, applied); }
+
 
 cudaError_t finalize(const double* partials, int nparts, double scale, double* out, int* status,
                      cudaStream_t s) {
@@ -452,16 +530,20 @@ nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device) {
     if (src_on_device) {
         // forward row transform straight from the caller's buffer
         if (g->p.precision == NLSE_FP64)
-            e = g->k64->row_forward((const double2*)src, (double2*)state, tab<double>(g, g->lay.tw), g->stream);
+            e = g->k64->row_forward((const double2*)src, (double2*)state, twiddles_fixed<double>(g->ws + g->lay.tw),
+                                    g->stream);
         else
-            e = g->k32->row_forward((const float2*)src, (float2*)state, tab<float>(g, g->lay.tw), g->stream);
+            e = g->k32->row_forward((const float2*)src, (float2*)state, twiddles_fixed<float>(g->ws + g->lay.tw),
+                                    g->stream);
     } else {
         e = cudaMemcpyAsync(state, src, bytes, cudaMemcpyHostToDevice, g->stream);
         if (e == cudaSuccess) {
             if (g->p.precision == NLSE_FP64)
-                e = g->k64->row_forward((const double2*)state, (double2*)state, tab<double>(g, g->lay.tw), g->stream);
+                e = g->k64->row_forward((const double2*)state, (double2*)state,
+                                        twiddles_fixed<double>(g->ws + g->lay.tw), g->stream);
             else
-                e = g->k32->row_forward((const float2*)state, (float2*)state, tab<float>(g, g->lay.tw), g->stream);
+                e = g->k32->row_forward((const float2*)state, (float2*)state,
+                                        twiddles_fixed<float>(g->ws + g->lay.tw), g->stream);
         }
     }
     if (e != cudaSuccess) return NLSE_ECUDA;
@@ -667,11 +749,12 @@ AdjLayout adj_layout_for(int n, int precision, int nsteps, int ckpt) {
     size_t o = 0;
     L.state = o;    o = align256(o + field);
     L.gam = o;      o = align256(o + field);
-    L.tw = o;       o = align256(o + (size_t)n * 16);
-    L.px = o;       o = align256(o + (size_t)n * 16);
-    L.py = o;       o = align256(o + (size_t)n * 16);
-    L.pxc = o;      o = align256(o + (size_t)n * 16);
-    L.pyc = o;      o = align256(o + (size_t)n * 16);
+    const size_t tb = table_bytes(n, precision);
+    L.tw = o;       o = align256(o + tb);
+    L.px = o;       o = align256(o + tb);
+    L.py = o;       o = align256(o + tb);
+    L.pxc = o;      o = align256(o + tb);
+    L.pyc = o;      o = align256(o + tb);
     L.seg = o;      o = align256(o + field * (size_t)ckpt);
     L.ckpt = o;     o = align256(o + field * (size_t)L.nck);
     L.target = o;   o = align256(o + (size_t)n * n * sizeof(double));
@@ -736,13 +819,18 @@ template <typename T> nlse_status adj_upload(nlse_adjoint* a) {
     propagator_tables(&a->p, px, py);
     const int ept = std::min(a->p.n, sizeof(T) == 4 ? 16 : 8);
     twiddle_table(a->p.n, ept, tw);
-    std::vector<double> pxc(px), pyc(py);
-    for (size_t i = 1; i < pxc.size(); i += 2) { pxc[i] = -pxc[i]; pyc[i] = -pyc[i]; }
-    const std::vector<double>* src[5] = {&tw, &px, &py, &pxc, &pyc};
+    const std::vector<double>* src[3] = {&tw, &px, &py};
+    const uint64_t ids[3] = {kTabTwiddle, kTabPx, kTabPy};
     const size_t off[5] = {a->lay.tw, a->lay.px, a->lay.py, a->lay.pxc, a->lay.pyc};
+    std::vector<T> rounded[5];
+    for (int t = 0; t < 3; ++t) round_table(*src[t], ids[t], rounded[t]);
+    // conjugated propagator tables: the conjugates of the same rounded values
+    for (int t = 3; t < 5; ++t) {
+        rounded[t] = rounded[t - 2];
+        for (size_t i = 1; i < rounded[t].size(); i += 2) rounded[t][i] = -rounded[t][i];
+    }
     for (int t = 0; t < 5; ++t) {
-        std::vector<T> r;
-        round_table(*src[t], r);
+        const std::vector<T>& r = rounded[t];
         if (cudaMemcpyAsync(a->ws + off[t], r.data(), r.size() * sizeof(T), cudaMemcpyHostToDevice,
                             a->stream) != cudaSuccess)
             return NLSE_ECUDA;
@@ -754,7 +842,8 @@ template <typename T> nlse_status adj_upload(nlse_adjoint* a) {
 template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* src, int on_device, double* loss) {
     const KernelSet<T>* ks = ASel<T>::ks(a);
     VT<T>* state = aat<T>(a, a->lay.state);
-    const WT<T>* tw = atab<T>(a, a->lay.tw);
+    const WT<T>* tw = twiddles_fixed<T>(a->ws + a->lay.tw);
+    const int n = a->p.n;
     const size_t fb = adj_field_bytes(a);
     cudaError_t e;
     if (on_device) {
@@ -771,10 +860,12 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
             cudaMemcpyAsync(a->ws + a->lay.ckpt + fb * (size_t)(s / a->ckpt), state, fb,
                             cudaMemcpyDeviceToDevice, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (ks->col_pass(state, state, tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
-                         rot_entry<T>(step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
+        const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
+        if (ks->col_pass(state, state, tws, table_at<T>(a->ws + a->lay.px, n, s),
+                         table_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols, nullptr,
+                         0u, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (ks->row_pass(state, state, tw, sc, partials, false, a->stream) != cudaSuccess) return NLSE_ECUDA;
+        if (ks->row_pass(state, state, tws, sc, partials, false, a->stream) != cudaSuccess) return NLSE_ECUDA;
     }
     double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
     if (ks->loss_seed(state, aat<T>(a, a->lay.gam), reinterpret_cast<const double*>(a->ws + a->lay.target),
@@ -796,7 +887,8 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
     const AdjCoef<T>& ac = ASel<T>::ac(a);
     VT<T>* state = aat<T>(a, a->lay.state);
     VT<T>* gam = aat<T>(a, a->lay.gam);
-    const WT<T>* tw = atab<T>(a, a->lay.tw);
+    const WT<T>* tw = twiddles_fixed<T>(a->ws + a->lay.tw);
+    const int n = a->p.n;
     const size_t fb = adj_field_bytes(a);
     double* partials = reinterpret_cast<double*>(a->ws + a->lay.partials);
     double* acc = reinterpret_cast<double*>(a->ws + a->lay.acc);
@@ -809,17 +901,21 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
                             a->stream) != cudaSuccess)
             return NLSE_ECUDA;
         for (int s = c0; s < c1; ++s) {  // recompute the segment, keeping T_s
-            if (ks->col_pass(state, seg(s - c0), tw, atab<T>(a, a->lay.px), atab<T>(a, a->lay.py),
-                             rot_entry<T>(step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
+            const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
+            if (ks->col_pass(state, seg(s - c0), tws, table_at<T>(a->ws + a->lay.px, n, s),
+                             table_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols,
+                             nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             if (s + 1 < c1 &&
-                ks->row_pass(seg(s - c0), state, tw, ac.sc, partials, false, a->stream) != cudaSuccess)
+                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
         }
-        for (int s = c1 - 1; s >= c0; --s) {  // reverse the segment
-            if (ks->adj_row(gam, seg(s - c0), tw, ac, acc, a->stream) != cudaSuccess) return NLSE_ECUDA;
-            if (ks->col_pass(gam, gam, tw, atab<T>(a, a->lay.pxc), atab<T>(a, a->lay.pyc),
-                             rot_entry<T>(-step_phase(s + 1)), a->cols, nullptr, 0u, a->stream) != cudaSuccess)
+        for (int s = c1 - 1; s >= c0; --s) {  // reverse the segment with the forward step's constants
+            const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
+            if (ks->adj_row(gam, seg(s - c0), tws, ac, acc, a->stream) != cudaSuccess) return NLSE_ECUDA;
+            if (ks->col_pass(gam, gam, tws, table_at<T>(a->ws + a->lay.pxc, n, s),
+                             table_at<T>(a->ws + a->lay.pyc, n, s), conj_of(rot_for_step<T>(s, nullptr)), a->cols,
+                             nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
         }
     }

@@ -22,11 +22,23 @@
 // Twiddles come from a pass-major table built in FP64 on the host: the pass
 // with stride NS and radix R owns (R-1) NS consecutive entries, entry
 // (r-1) NS + k holding W_{NS R}^{r k}.  A warp's loads for one r are then
-// contiguous, and one base address per pass serves all r.  In FP32 every twiddle, radix constant and propagator factor is
-// held as an unevaluated pair hi + lo (hi = fl32(w), lo = fl32(w - hi)) and
-// multiplied with FMA chains, so that the factor is exact to O(eps^2): the
-// same factors are applied at every z step, and a rounded factor would act as
-// a fixed operator error that accumulates linearly over thousands of steps.
+// contiguous, and one base address per pass serves all r.
+//
+// Rounding of the table factors (FP32).  The same twiddles and propagator
+// factors are applied at every z step, so a factor rounded to FP32 once would
+// act as a fixed operator error that adds up linearly over thousands of steps.
+// Instead each table exists in kDither copies whose entries are rounded up or
+// down with a dither: entry e of copy d is rounded up when the fraction of an
+// FP32 unit by which the exact value exceeds its lower FP32 neighbour is above
+// ((d + o_e) mod kDither + 1/2) / kDither, o_e a fixed pseudo-random offset per
+// entry and component, and step k uses copy k mod kDither.  The mean factor
+// over every kDither steps is then exact to 1/(2 kDither) of an FP32 unit while
+// each multiply stays a plain FP32 complex product.  The three radix-16
+// constants, applied to most values of every pass and all with the same
+// rounding error, are kept exact to O(eps^2) as unevaluated FP32 pairs
+// (hi + lo, FMA chains): rounded or dithered, their common magnitude error
+// changes the power of the whole field every step.  In FP64 every factor is the
+// rounded value itself.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -60,25 +72,40 @@ template <typename V> __device__ __forceinline__ V cscale(V a, typename real_of<
     return mk<V>(a.x * s, a.y * s);
 }
 
-// table entry of twiddles and propagator factors: (hi.re, hi.im, lo.re, lo.im)
-// in FP32, the value itself in FP64
+// copies of each FP32 table (step k uses copy k mod kDither; see above)
+constexpr int kDither = 16;
+
+// table entry of twiddles and propagator factors: one complex value
 template <typename T> struct tab_of;
-template <> struct tab_of<float> { using type = float4; };
+template <> struct tab_of<float> { using type = float2; };
 template <> struct tab_of<double> { using type = double2; };
 
 // Table load through the read-only path at a compile-time byte offset from a
 // per-pass base pointer.  Issued as volatile asm with the offset as an
 // immediate: one base register serves every r of a pass, and the forward and
 // inverse transforms of a kernel cannot share (and keep live) the loaded values.
-template <int OFF> __device__ __forceinline__ float4 ldtab(const float4* base) {
-    float4 r;
-    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(base), "n"(OFF * 16));
+template <int OFF> __device__ __forceinline__ float2 ldtab(const float2* base) {
+    float2 r;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2+%3];" : "=f"(r.x), "=f"(r.y) : "l"(base), "n"(OFF * 8));
     return r;
 }
 template <int OFF> __device__ __forceinline__ double2 ldtab(const double2* base) {
     double2 r;
     asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2+%3];" : "=d"(r.x), "=d"(r.y) : "l"(base), "n"(OFF * 16));
+    return r;
+}
+
+// Load of one table entry through the read-only path at its point in the
+// program: volatile, so that the compiler does not hoist a kernel's table loads
+// above the transforms (where they would hold registers throughout).
+__device__ __forceinline__ float2 ldent(const float2* p) {
+    float2 r;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ double2 ldent(const double2* p) {
+    double2 r;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
     return r;
 }
 
@@ -90,48 +117,12 @@ template <int I, int END, typename F> __device__ __forceinline__ void static_for
     }
 }
 
-// a * w (CONJ = false) or a * conj(w) (CONJ = true), w an exact-to-eps^2 table entry
-template <bool CONJ> __device__ __forceinline__ float2 twmul(float2 a, float4 w) {
-    float2 r;
-    if constexpr (!CONJ) {
-        r.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, fmaf(a.x, w.z, -a.y * w.w)));
-        r.y = fmaf(a.x, w.y, fmaf(a.y, w.x, fmaf(a.x, w.w, a.y * w.z)));
-    } else {
-        r.x = fmaf(a.x, w.x, fmaf(a.y, w.y, fmaf(a.x, w.z, a.y * w.w)));
-        r.y = fmaf(a.y, w.x, fmaf(-a.x, w.y, fmaf(a.y, w.z, -a.x * w.w)));
-    }
-    return r;
-}
-template <bool CONJ> __device__ __forceinline__ double2 twmul(double2 a, double2 w) {
+// a * w (CONJ = false) or a * conj(w) (CONJ = true)
+template <bool CONJ, typename V> __device__ __forceinline__ V twmul(V a, V w) {
     return CONJ ? cmulc(a, w) : cmul(a, w);
 }
-
-// product of two table entries, as a table entry: in FP32 the hi/lo pairs are
-// multiplied with error-free transformations (exact products by FMA, TwoSum) so
-// that the result is again exact to O(eps^2)
-__device__ __forceinline__ float two_sum_lo(float a, float b, float s) {
-    const float bb = s - a;
-    return (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ float4 tabmul(float4 a, float4 b) {
-    // real: ah.x bh.x - ah.y bh.y (+ first-order lo terms)
-    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
-    const float p2 = -a.y * b.y, e2 = fmaf(-a.y, b.y, -p2);
-    const float sr = p1 + p2, er = two_sum_lo(p1, p2, sr);
-    const float lr = er + e1 + e2 + (a.x * b.z + a.z * b.x - a.y * b.w - a.w * b.y);
-    // imaginary: ah.x bh.y + ah.y bh.x (+ first-order lo terms)
-    const float q1 = a.x * b.y, f1 = fmaf(a.x, b.y, -q1);
-    const float q2 = a.y * b.x, f2 = fmaf(a.y, b.x, -q2);
-    const float si = q1 + q2, ei = two_sum_lo(q1, q2, si);
-    const float li = ei + f1 + f2 + (a.x * b.w + a.z * b.y + a.y * b.z + a.w * b.x);
-    float4 r;
-    r.x = sr + lr;
-    r.z = lr - (r.x - sr);
-    r.y = si + li;
-    r.w = li - (r.y - si);
-    return r;
-}
-__device__ __forceinline__ double2 tabmul(double2 a, double2 b) { return cmul(a, b); }
+// product of two table entries
+template <typename V> __device__ __forceinline__ V tabmul(V a, V b) { return cmul(a, b); }
 
 // multiply by W_4^1: -i in the forward transform, +i in the inverse
 template <bool INV, typename V> __device__ __forceinline__ V rot4(V a) {

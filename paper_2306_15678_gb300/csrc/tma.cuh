@@ -145,14 +145,15 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     V* sm = smem + c * LS;
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
+        if (half == 1) conj_all(v);  // second round: B_y = conj(F_y(conj(.)))
         fft_stockham<V, N, E, false>(v, sm, tw, j);
         if (half == 0) {
-            const auto pxc = tabmul(__ldg(&px[col]), rot);
+            const auto pxc = tabmul(ldent(px + col), rot);
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = twmul<false>(twmul<false>(v[m], pxc), __ldg(&py[j + m * TL]));
+            for (int m = 0; m < E; ++m) v[m] = twmul<false>(twmul<false>(v[m], pxc), ldent(py + j + m * TL));
         }
-        conj_all(v);  // second round: conj(F_y(conj(.))) = B_y
     }
+    conj_all(v);
 #pragma unroll
     for (int m = 0; m < E; ++m) stage[(j + m * TL) * C + c] = v[m];
     fence_proxy_async_smem();
