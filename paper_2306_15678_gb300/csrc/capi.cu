@@ -22,6 +22,7 @@ using namespace nlse;
 namespace {
 
 constexpr int kHistCap = 4096;
+constexpr int kDiagBatch = 64;  // diagnostic steps whose per-block partials are finalised together
 constexpr double kIref = 1.0e13;  // W/cm^2: scale of the screen's intensity variable
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
@@ -41,7 +42,7 @@ int log2_exact(int n) {
 }
 
 struct Layout {
-    size_t state, aux, tw, px, py, partials, hist, readout, status, total;
+    size_t state, aux, tw, px, py, partials, diag, hist, readout, status, total;
 };
 
 Layout layout_for(int n, int precision) {
@@ -56,6 +57,7 @@ Layout layout_for(int n, int precision) {
     L.px = o;       o = align256(o + tb);
     L.py = o;       o = align256(o + tb);
     L.partials = o; o = align256(o + (size_t)n * 2 * sizeof(double));
+    L.diag = o;     o = align256(o + (size_t)kDiagBatch * n * 2 * sizeof(double));
     L.hist = o;     o = align256(o + (size_t)kHistCap * 2 * sizeof(double));
     L.readout = o;  o = align256(o + 2 * sizeof(double));
     L.status = o;   o = align256(o + sizeof(int));
@@ -238,7 +240,8 @@ struct nlse_grid {
     unsigned char* ws;
     Layout lay;
     int64_t steps;
-    int64_t hist_count;
+    int64_t hist_count;  // diagnostic steps finalised into the history ring
+    int diag_pending;    // diagnostic steps recorded in the diag buffer, not yet finalised
     int loaded;
     int cols;  // column tile of the column pass
     unsigned debug_extra_tx;  // test hook of the staged column pass (NLSE_DEBUG_COL_EXTRA_TX), 0 in use
@@ -327,6 +330,22 @@ template <typename T> VT<T> unrot_value(double theta) {
 }
 inline double* dat(nlse_grid* g, size_t off) { return reinterpret_cast<double*>(g->ws + off); }
 
+// Finalise the pending diagnostic steps into the history ring (one block per step).
+template <typename T> nlse_status flush_diag(nlse_grid* g) {
+    if (g->diag_pending == 0) return NLSE_OK;
+    const double dx = g->p.L / g->p.n;
+    k_finalize_batch<<<g->diag_pending, 256, 0, g->stream>>>(
+        dat(g, g->lay.diag), Sel<T>::ks(g)->row_blocks, dx * dx, dat(g, g->lay.hist), (long long)g->hist_count,
+        kHistCap, reinterpret_cast<int*>(g->ws + g->lay.status));
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    g->hist_count += g->diag_pending;
+    g->diag_pending = 0;
+    return NLSE_OK;
+}
+nlse_status flush_diag_any(nlse_grid* g) {
+    return g->p.precision == NLSE_FP64 ? flush_diag<double>(g) : flush_diag<float>(g);
+}
+
 template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_t* ev = nullptr) {
     const KernelSet<T>* ks = Sel<T>::ks(g);
     VT<T>* field = at<T>(g, g->lay.state);
@@ -347,15 +366,12 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 1], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const bool diag = g->p.diag_every > 0 && ((g->steps + 1) % g->p.diag_every) == 0;
-        e = ks->row_pass(field, field, tw, Sel<T>::sc(g), partials, diag, g->stream);
+        // a diagnostic step leaves its per-block partials in the next slot of the
+        // diag buffer; a full buffer is finalised into the history in one launch
+        double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * ks->row_blocks;
+        e = ks->row_pass(field, field, tw, Sel<T>::sc(g), diag ? slot : partials, diag, g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
-        if (diag) {
-            double* slot = dat(g, g->lay.hist) + 2 * (g->hist_count % kHistCap);
-            k_finalize<<<1, 256, 0, g->stream>>>(partials, ks->row_blocks, dx * dx, slot,
-                                                 reinterpret_cast<int*>(g->ws + g->lay.status));
-            if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
-            ++g->hist_count;
-        }
+        if (diag && ++g->diag_pending == kDiagBatch && flush_diag<T>(g) != NLSE_OK) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
         ++g->steps;
     }
@@ -549,6 +565,7 @@ nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device) {
     if (e != cudaSuccess) return NLSE_ECUDA;
     g->steps = 0;
     g->hist_count = 0;
+    g->diag_pending = 0;
     g->theta = 0.0;
     g->loaded = 1;
     return NLSE_OK;
@@ -683,6 +700,7 @@ nlse_status nlse_read_field(nlse_grid* g, void* dst, int dst_on_device) {
 
 nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capacity, int32_t* count) {
     if (!g || !count || capacity < 0) return NLSE_EINVAL;
+    if (flush_diag_any(g) != NLSE_OK) return NLSE_ECUDA;
     const int64_t have = g->hist_count < kHistCap ? g->hist_count : kHistCap;
     const int64_t first = g->hist_count - have;
     std::vector<double> buf(2 * (size_t)kHistCap);

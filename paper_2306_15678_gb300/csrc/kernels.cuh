@@ -44,12 +44,19 @@ template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
 // below 2e-9 and 2e-10.  Returning cos - 1 instead of cos keeps the rounding
 // error of the small screen phases relative to the phase, not to 1.  The
 // reduction stays accurate to |x| ~ 1e5 rad; beyond (a diverged march) the
-// reduced argument is clamped so the results stay bounded.
+// reduced argument is clamped so the results stay bounded.  When every lane of
+// the warp has |x| <= pi/4 (per-step screen phases usually are) the reduction
+// and the quadrant fix-up are skipped: they would leave x unchanged, so the
+// results are the same bits either way.
 __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
-    const float q = rintf(x * 0.636619772367581343f);   // x / (pi/2)
-    float r = fmaf(-q, 1.57079637050628662f, x);        // pi/2 rounded to FP32
-    r = fmaf(-q, -4.37113900018624283e-8f, r);          // pi/2 - fl32(pi/2)
-    r = fminf(fmaxf(r, -0.7853982f), 0.7853982f);
+    const bool small = __all_sync(__activemask(), fabsf(x) <= 0.7853982f);  // uniform per warp
+    float r = x, q = 0.0f;
+    if (!small) {
+        q = rintf(x * 0.636619772367581343f);           // x / (pi/2)
+        r = fmaf(-q, 1.57079637050628662f, x);           // pi/2 rounded to FP32
+        r = fmaf(-q, -4.37113900018624283e-8f, r);       // pi/2 - fl32(pi/2)
+        r = fminf(fmaxf(r, -0.7853982f), 0.7853982f);
+    }
     const float r2 = r * r;
     float ps = fmaf(r2, 2.75573192239858906e-6f, -1.98412698412698413e-4f);
     ps = fmaf(r2, ps, 8.33333333333333333e-3f);
@@ -60,6 +67,11 @@ __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
     pc = fmaf(r2, pc, 4.16666666666666667e-2f);
     pc = fmaf(r2, pc, -0.5f);
     const float cr1 = r2 * pc;                           // cos r - 1
+    if (small) {
+        *s = sr;
+        *cm1 = cr1;
+        return;
+    }
     // x = r + quad pi/2: quad 0 (sr, cr1), 1 (1 + cr1, -sr - 1),
     // 2 (-sr, -2 - cr1), 3 (-1 - cr1, sr - 1)
     const int quad = ((int)q) & 3;
@@ -70,13 +82,15 @@ __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
 }
 
 // exp(x) - 1: Taylor polynomial to x^5 for |x| < 1/16 (error < 3e-11 relative),
-// expf(x) - 1 beyond
+// expf(x) - 1 beyond; expf is skipped when no lane of the warp needs it
 __device__ __forceinline__ float expm1_(float x) {
     float p = fmaf(x, 8.33333333333333333e-3f, 4.16666666666666667e-2f);
     p = fmaf(x, p, 1.66666666666666667e-1f);
     p = fmaf(x, p, 0.5f);
     const float small = fmaf(x * x, p, x);
-    return fabsf(x) < 0.0625f ? small : expf(x) - 1.0f;
+    const bool in_range = fabsf(x) < 0.0625f;
+    if (__all_sync(__activemask(), in_range)) return small;
+    return in_range ? small : expf(x) - 1.0f;
 }
 
 // U = v exp(s(|v|^2)) (Eq. 2: screen evaluated on the field entering it)
@@ -166,34 +180,109 @@ __device__ __forceinline__ void block_partials(T tsum, T tmax, double* __restric
     }
 }
 
-// Deterministic FP64 reduction of nparts (sum, max) pairs; one block of 256.
-// out[0] = scale * sum, out[1] = max; flags NONFINITE in *status.
-static __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nparts,
-                                                  double scale, double* __restrict__ out,
-                                                  int* __restrict__ status) {
-    __shared__ double ss[256];
-    __shared__ double sm[256];
-    double s = 0.0, m = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += 256) {
-        s += partials[2 * i];
-        m = fmax(m, partials[2 * i + 1]);
+// FP32 values: the block's tree in FP32 (FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this GPU: even a one-thread FP64 loop per block
+// holds up the block's end), the sum over all blocks (k_finalize) in FP64, in
+// a fixed order.  The FP32 tree adds about 13 roundings to each block sum;
+// they are unbiased and independent between blocks.
+template <>
+__device__ __forceinline__ void block_partials<float>(float tsum, float tmax, double* __restrict__ partials) {
+    __shared__ float red_s[32];
+    __shared__ float red_m[32];
+    if (blockDim.x < 32) {  // tiny grids: blocks narrower than a warp
+        red_s[threadIdx.x] = tsum;
+        red_m[threadIdx.x] = tmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float ss = 0.0f, mm = 0.0f;
+            for (int t = 0; t < (int)blockDim.x; ++t) { ss += red_s[t]; mm = fmaxf(mm, red_m[t]); }
+            partials[2 * blockIdx.x] = (double)ss;
+            partials[2 * blockIdx.x + 1] = (double)mm;
+        }
+        return;
     }
-    ss[threadIdx.x] = s;
-    sm[threadIdx.x] = m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red_s[warp] = tsum; red_m[warp] = tmax; }
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            ss[threadIdx.x] += ss[threadIdx.x + o];
-            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        float ss = 0.0f, mm = 0.0f;
+        for (int w = 0; w < nw; ++w) { ss += red_s[w]; mm = fmaxf(mm, red_m[w]); }
+        partials[2 * blockIdx.x] = (double)ss;
+        partials[2 * blockIdx.x + 1] = (double)mm;
+    }
+}
+
+// Final FP64 reduction of nparts (sum, max) partials by one whole block, in
+// an order fixed by the block size B: thread t sums partials t, t + B, t + 2B,
+// ... (sixteen loads in flight at a time: the loop is latency-bound otherwise),
+// then a shared-memory tree in scratch (2 B doubles).  out[0] = scale * sum,
+// out[1] = max; bit 0 of *status flags a non-finite result.  Partials written
+// by other blocks of the same launch are read from L2.
+__device__ __forceinline__ void block_finalize(const double* partials, int nparts, double scale, double* out,
+                                               int* status, double* scratch) {
+    constexpr int PER = 16;
+    const double2* pp = reinterpret_cast<const double2*>(partials);
+    const int B = blockDim.x;
+    double s = 0.0, m = 0.0;
+    for (int base = threadIdx.x; base < nparts; base += B * PER) {
+        double2 buf[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int i = base + q * B;
+            buf[q] = i < nparts ? __ldcg(&pp[i]) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            s += buf[q].x;
+            m = fmax(m, buf[q].y);
+        }
+    }
+    double* fs = scratch;
+    double* fm = scratch + B;
+    fs[threadIdx.x] = s;
+    fm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (o < B && (int)threadIdx.x < o && (int)threadIdx.x + o < B) {
+            fs[threadIdx.x] += fs[threadIdx.x + o];
+            fm[threadIdx.x] = fmax(fm[threadIdx.x], fm[threadIdx.x + o]);
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double p = ss[0] * scale;
+        const double p = fs[0] * scale;
         out[0] = p;
-        out[1] = sm[0];
-        if (!isfinite(p) || !isfinite(sm[0])) *status |= 1;  // bit 0: non-finite
+        out[1] = fm[0];
+        if (!isfinite(p) || !isfinite(fm[0])) *status |= 1;  // bit 0: non-finite
     }
+}
+
+// Deterministic FP64 reduction of nparts (sum, max) pairs: block_finalize by
+// one block of 256 (readouts and losses).
+static __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nparts,
+                                                  double scale, double* __restrict__ out,
+                                                  int* __restrict__ status) {
+    __shared__ double scratch[512];
+    block_finalize(partials, nparts, scale, out, status, scratch);
+}
+
+// The same for `count` recorded steps at once (one block each): step i's
+// partials start at partials + 2 i nparts and its (power, peak) go to slot
+// (first + i) mod cap of the history ring.  The march records the per-block
+// partials of its diagnostic steps and finalises them in batches, off the
+// path of the step.
+static __global__ void __launch_bounds__(256) k_finalize_batch(const double* __restrict__ partials, int nparts,
+                                                        double scale, double* __restrict__ hist,
+                                                        long long first, int cap, int* __restrict__ status) {
+    __shared__ double scratch[512];
+    const long long slot = (first + blockIdx.x) % cap;
+    block_finalize(partials + 2 * (size_t)blockIdx.x * nparts, nparts, scale, hist + 2 * slot, status, scratch);
 }
 
 // ----------------------------------------------------------------- passes --
