@@ -80,9 +80,12 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
                  ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
 }
-__device__ __forceinline__ void tma_store_commit_and_wait() {
+// commit the block's bulk stores and wait until they have read their source:
+// the shared memory may then be released (the writes complete on their own,
+// before the kernel does)
+__device__ __forceinline__ void tma_store_commit_and_wait_read() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 // make this thread's generic-proxy shared-memory writes visible to bulk copies
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -161,7 +164,7 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     if (threadIdx.x == 0) {
 #pragma unroll 1
         for (int b = 0; b < BOXES; ++b) tma_store_2d(&mstore, x, b * kTmaBoxRows, stage + b * kTmaBoxRows * C);
-        tma_store_commit_and_wait();
+        tma_store_commit_and_wait_read();
     }
 }
 
