@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--large-adjoint-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -273,6 +274,52 @@ def bench_adjoint(dev) -> dict:
             "grad_finite": bool(np.all(np.isfinite(dth)))}
 
 
+def bench_large_adjoint(dev, nsteps: int) -> dict:
+    """A sample of the large batched adjoint: one of its 8192^2 beams (16 cm
+    window, w0 = 3 cm, P = 500 P_cr, full screen), nsteps steps with
+    ceil(sqrt(nsteps)) checkpointing, FP32 field, FP64 loss and gradients;
+    against the plain forward march of the same steps."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2306_15678_gb300 import beams, configs
+    from paper_2306_15678_gb300.adjoint import AdjointMarch
+    from paper_2306_15678_gb300.grid import Grid
+    cfg = configs.cfg_large_adjoint(1)[0]
+    n = cfg["n"]
+    k = configs.sqrt_checkpoint(nsteps)
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    D = np.abs(beams.make_field(dict(cfg, beam=dict(cfg["beam"], w0=3.06, seed=5099)))) ** 2
+    with Grid(cfg, precision="fp32", device=dev) as g:
+        g.load(U0).step(3)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.step(nsteps)
+        g.power()
+        fwd = time.perf_counter() - t0
+    fit = AdjointMarch(cfg, nsteps, k, precision="fp32", device=dev)
+    try:
+        fit.set_target(D)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        J = fit.forward(U0)
+        t1 = time.perf_counter()
+        dth, _ = fit.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        ws = fit.ws_bytes
+    finally:
+        fit.close()
+    return {"workload": f"1 of 8 beams {n}x{n}, {nsteps} of 3000 steps, checkpoint every {k} (sqrt), FP32, "
+                        "6 gains + input field",
+            "forward_march_ms": fwd * 1e3, "adjoint_forward_ms": (t1 - t0) * 1e3,
+            "adjoint_backward_ms": (t2 - t1) * 1e3, "adjoint_over_forward": (t2 - t0) / fwd,
+            "gradient_pt_steps_per_s": n * n * nsteps / (t2 - t0), "workspace_gib": ws / 2 ** 30,
+            "loss": J, "grad_finite": bool(np.all(np.isfinite(dth)))}
+
+
 def run_reference(args, world, rank, cfg):
     if rank != 0:
         return
@@ -426,6 +473,7 @@ def main():
 
     batch = None if args.no_batch else bench_batch(args, dev, peak_gbs)
     adjoint = None if args.no_adjoint else bench_adjoint(dev)
+    large_adjoint = None if args.no_adjoint else bench_large_adjoint(dev, args.large_adjoint_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -439,7 +487,7 @@ def main():
             "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
-            "batch": batch, "adjoint": adjoint,
+            "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -116,6 +116,12 @@ def cfg_large_adjoint(nbeams: int = 8) -> list:
     return out
 
 
+def sqrt_checkpoint(nsteps: int) -> int:
+    """Checkpoint spacing ceil(sqrt(M)) for an M-step adjoint: about 2 sqrt(M)
+    stored fields (checkpoints plus one recomputed segment) instead of M."""
+    return max(1, math.ceil(math.sqrt(int(nsteps))))
+
+
 def scaled(cfg: dict, n: int, nsteps: int | None = None, L: float | None = None) -> dict:
     """Same physics and beam on another grid size (for oracle-sized parity runs)."""
     d = dict(cfg)

@@ -66,3 +66,21 @@ def test_create_rejects_bad_workspace_before_any_launch():
     with pytest.raises(capi.NlseError) as ei:
         capi.nlse_create(p, 0, 256 * 1024 + 8, 1 << 40)  # misaligned
     assert ei.value.status == capi.NLSE_EINVAL
+
+
+def test_large_adjoint_fits_with_sqrt_checkpointing():
+    """8192^2 FP32, 3000 steps (the large batched adjoint): checkpointing every
+    ceil(sqrt(3000)) = 55 steps keeps one beam's workspace near 2 sqrt(M) fields
+    (~56 GiB), so several beams fit in the GPU's memory at once; storing every
+    step would need 3000 fields (1.5 TiB)."""
+    cfg = configs.cfg_large_adjoint(1)[0]
+    p = make_params(cfg)
+    M = cfg["nsteps"]
+    k = configs.sqrt_checkpoint(M)
+    assert k == 55
+    field = 8192 * 8192 * 8
+    ws = capi.nlse_adjoint_workspace_size(p, M, k)
+    nck = -(-M // k)
+    assert (k + nck) * field <= ws <= (k + nck + 6) * field
+    assert ws < 60 * 2 ** 30
+    assert capi.nlse_adjoint_workspace_size(p, M, M) > 25 * ws

@@ -179,3 +179,43 @@ def test_sparse_grid_fit_full_run_is_deterministic_and_finite():
     b = run_gpu(cfg, U0, D, 400, 40, "fp32")
     assert np.isfinite(a[0]) and np.all(np.isfinite(a[1])) and np.all(np.isfinite(a[2]))
     assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_large_grid_adjoint_8192_against_differences():
+    """The large batched adjoint's grid (8192^2, 16 cm window, w0 = 3 cm,
+    P = 500 P_cr), a few steps with sqrt(M) checkpointing: the FP32 gradient
+    against central differences of the FP64 GPU forward (Richardson, h = 1e-4)
+    for the six gains, and dJ/dU0 along a random direction."""
+    cfg = configs.cfg_large_adjoint(1)[0]
+    M = 6
+    k = configs.sqrt_checkpoint(M)
+    U0 = beams.make_field(cfg).astype(np.complex64).astype(np.complex128)
+    other = dict(cfg, beam=dict(cfg["beam"], w0=cfg["beam"]["w0"] * 1.02, seed=5099))
+    D = np.abs(beams.make_field(other)) ** 2
+    _, t, g = run_gpu(cfg, U0, D, M, k, "fp32")
+    assert np.all(np.isfinite(t)) and np.all(np.isfinite(g))
+    fit = AdjointMarch(cfg, M, k, precision="fp64")
+    fit.set_target(D)
+    try:
+        def J(theta=None, U=U0):
+            fit.set_theta(theta if theta is not None else cfg["theta"])
+            return fit.forward(U)
+
+        h = 1e-4
+        for j in range(6):
+            def cd(hh):
+                tp = np.array(cfg["theta"], float); tp[j] += hh
+                tm = np.array(cfg["theta"], float); tm[j] -= hh
+                return (J(tp) - J(tm)) / (2 * hh)
+            fd = (4 * cd(h / 2) - cd(h)) / 3
+            assert abs(t[j] - fd) <= 1e-3 * max(abs(fd), 1e-3 * np.max(np.abs(t))), (j, t[j], fd)
+        rng = np.random.default_rng(6)
+        d = (rng.standard_normal(U0.shape) + 1j * rng.standard_normal(U0.shape)) * np.abs(U0).max()
+        hh = 2e-5
+        def cdu(e):
+            return (J(None, U0 + e * d) - J(None, U0 - e * d)) / (2 * e)
+        fd = (4 * cdu(hh / 2) - cdu(hh)) / 3
+        an = float(np.real(np.vdot(g, d)))
+        assert abs(an - fd) <= 1e-3 * abs(fd), (an, fd)
+    finally:
+        fit.close()
