@@ -227,11 +227,16 @@ template <typename T, int N> constexpr int col_mask() {
            (col_tma_ok<T, N, 8>() ? 256 : 0) | (col_tma_ok<T, N, 16>() ? 512 : 0);
 }
 
-// default column tile: the widest valid tile of at most 512 threads, unless
-// its row segments are shorter than one 32-byte sector, in which case the
-// narrowest valid tile that fills a sector (else the widest valid tile)
+// default column tile: the staged variant with 16-byte tile rows (two
+// complex64 or one complex128 column) where it exists -- the fastest or
+// within 2 % of the fastest tile at every size measured on GB300 --, else the
+// widest valid tile of at most 512 threads, unless its row segments are
+// shorter than one 32-byte sector, in which case the narrowest valid tile that
+// fills a sector (else the widest valid tile)
 template <typename T, int N> constexpr int col_default() {
     constexpr int cs = 2 * (int)sizeof(T);
+    constexpr int staged = 16 / cs;  // columns per 16-byte tile row
+    if (col_tma_ok<T, N, staged>()) return kColTma | staged;
     int best = 0;
     for (int i = 0; i < 5; ++i) {
         const int c = kColOptions[i];
