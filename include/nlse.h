@@ -144,8 +144,10 @@ nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double
 /* Column tile of the column pass: a width of 1, 2, 4, 8 or 16 columns per
  * block, or'ed with NLSE_COL_TMA for the variant that moves the tile between
  * global and shared memory with bulk tensor copies (cp.async.bulk.tensor,
- * 256-row boxes) instead of per-thread loads and stores; that variant exists
- * where a tile row is a multiple of 16 bytes and n a multiple of 256.
+ * boxes of 512 rows) instead of per-thread loads and stores; that variant
+ * exists for n >= 512 (default there: one column per block).  The field
+ * between the passes is stored with the two rows of each row pair interleaved
+ * element by element, so that one column is a sequence of 16-byte units.
  * NLSE_EUNSUPPORTED for a tile this size cannot use.  Chosen by the
  * autotuner; results do not depend on it, bit for bit.  A bounded wait (1 s)
  * of the staged variant that runs out makes the block skip its tile and sets

@@ -109,7 +109,7 @@ k_loss_seed(const typename vec2<T>::type* __restrict__ state, typename vec2<T>::
     V* sm = smem + g * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = state[row * N + j + m * TL];
+    for (int m = 0; m < E; ++m) v[m] = state[sidx<N>(row, j + m * TL)];
     fft_stockham<V, N, E, true>(v, sm, tw, j);
     const T inv = (T)1 / (T)N;
     double part = 0.0;
@@ -124,7 +124,7 @@ k_loss_seed(const typename vec2<T>::type* __restrict__ state, typename vec2<T>::
     }
     fft_stockham<V, N, E, false>(v, sm, tw, j);
 #pragma unroll
-    for (int m = 0; m < E; ++m) gam[row * N + j + m * TL] = v[m];
+    for (int m = 0; m < E; ++m) gam[sidx<N>(row, j + m * TL)] = v[m];
     block_partials<double>(part, 0.0, partials);
 }
 
@@ -146,10 +146,10 @@ k_adj_row(typename vec2<T>::type* __restrict__ gam, const typename vec2<T>::type
     V* sm = smem + g * LS;
     V vt[E], gw[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) vt[m] = tn[row * N + j + m * TL];
+    for (int m = 0; m < E; ++m) vt[m] = tn[sidx<N>(row, j + m * TL)];
     fft_stockham<V, N, E, true>(vt, sm, tw, j);   // v = B_x T
 #pragma unroll
-    for (int m = 0; m < E; ++m) gw[m] = gam[row * N + j + m * TL];
+    for (int m = 0; m < E; ++m) gw[m] = gam[sidx<N>(row, j + m * TL)];
     fft_stockham<V, N, E, true>(gw, sm, tw, j);   // G_U = B_x G_S
     T th[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
     if (ac.sc.active) {
@@ -174,7 +174,7 @@ k_adj_row(typename vec2<T>::type* __restrict__ gam, const typename vec2<T>::type
     }
     fft_stockham<V, N, E, false>(gw, sm, tw, j);  // G_T = F_x G_v
 #pragma unroll
-    for (int m = 0; m < E; ++m) gam[row * N + j + m * TL] = gw[m];
+    for (int m = 0; m < E; ++m) gam[sidx<N>(row, j + m * TL)] = gw[m];
     block_accumulate6<T>(th, acc);
 }
 

@@ -472,8 +472,10 @@ nlse_status nlse_batch_load_field(nlse_batch* B, int32_t beam, const void* src, 
     if (src_on_device) {
         e = ks->row_forward((const float2*)src, f, tw, B->stream);
     } else {
-        e = cudaMemcpyAsync(f, src, (size_t)n * n * 8, cudaMemcpyHostToDevice, B->stream);
-        if (e == cudaSuccess) e = ks->row_forward(f, f, tw, B->stream);
+        // staged in the scratch buffer: the state layout differs from the rows'
+        float2* rows = reinterpret_cast<float2*>(B->ws + B->lay.scratch);
+        e = cudaMemcpyAsync(rows, src, (size_t)n * n * 8, cudaMemcpyHostToDevice, B->stream);
+        if (e == cudaSuccess) e = ks->row_forward(rows, f, tw, B->stream);
     }
     return e == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
 }

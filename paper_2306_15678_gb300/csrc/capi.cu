@@ -542,25 +542,22 @@ nlse_status nlse_load_field(nlse_grid* g, const void* src, int src_on_device) {
     const size_t cs = g->p.precision == NLSE_FP64 ? 16 : 8;
     const size_t bytes = (size_t)g->p.n * g->p.n * cs;
     void* state = g->ws + g->lay.state;
-    cudaError_t e;
-    if (src_on_device) {
-        // forward row transform straight from the caller's buffer
+    // the forward row transform reads the row-major field (the caller's device
+    // buffer, or the host field staged in the scratch buffer) and writes the
+    // state, whose layout differs: never in place
+    const void* rows = src;
+    cudaError_t e = cudaSuccess;
+    if (!src_on_device) {
+        rows = g->ws + g->lay.aux;
+        e = cudaMemcpyAsync(g->ws + g->lay.aux, src, bytes, cudaMemcpyHostToDevice, g->stream);
+    }
+    if (e == cudaSuccess) {
         if (g->p.precision == NLSE_FP64)
-            e = g->k64->row_forward((const double2*)src, (double2*)state, twiddles_fixed<double>(g->ws + g->lay.tw),
+            e = g->k64->row_forward((const double2*)rows, (double2*)state, twiddles_fixed<double>(g->ws + g->lay.tw),
                                     g->stream);
         else
-            e = g->k32->row_forward((const float2*)src, (float2*)state, twiddles_fixed<float>(g->ws + g->lay.tw),
+            e = g->k32->row_forward((const float2*)rows, (float2*)state, twiddles_fixed<float>(g->ws + g->lay.tw),
                                     g->stream);
-    } else {
-        e = cudaMemcpyAsync(state, src, bytes, cudaMemcpyHostToDevice, g->stream);
-        if (e == cudaSuccess) {
-            if (g->p.precision == NLSE_FP64)
-                e = g->k64->row_forward((const double2*)state, (double2*)state,
-                                        twiddles_fixed<double>(g->ws + g->lay.tw), g->stream);
-            else
-                e = g->k32->row_forward((const float2*)state, (float2*)state,
-                                        twiddles_fixed<float>(g->ws + g->lay.tw), g->stream);
-        }
     }
     if (e != cudaSuccess) return NLSE_ECUDA;
     g->steps = 0;
@@ -866,9 +863,10 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
     cudaError_t e;
     if (on_device) {
         e = ks->row_forward((const VT<T>*)src, state, tw, a->stream);
-    } else {
-        e = cudaMemcpyAsync(state, src, fb, cudaMemcpyHostToDevice, a->stream);
-        if (e == cudaSuccess) e = ks->row_forward(state, state, tw, a->stream);
+    } else {  // the host field is staged in gam (free until the backward sweep)
+        VT<T>* rows = aat<T>(a, a->lay.gam);
+        e = cudaMemcpyAsync(rows, src, fb, cudaMemcpyHostToDevice, a->stream);
+        if (e == cudaSuccess) e = ks->row_forward(rows, state, tw, a->stream);
     }
     if (e != cudaSuccess) return NLSE_ECUDA;
     const ScreenCoef<T>& sc = ASel<T>::ac(a).sc;

@@ -99,11 +99,12 @@ cudaError_t launch_col_c(const typename vec2<T>::type* src, typename vec2<T>::ty
     }
 }
 
-// Tensor map of an n x n complex field as n rows of 2n words (4-byte words
-// for complex64, 8-byte for complex128: the copies move bits, no conversion),
-// boxes of 2C words x 256 rows.  cuTensorMapEncodeTiled is a host-only driver
-// call, reached through the runtime's entry-point query so that the library
-// needs no link to libcuda.
+// Tensor map of an n x n complex state (state layout, see sidx) as n/2 row
+// pairs x n columns x 4 words (4-byte words for complex64, 8-byte for
+// complex128: the copies move bits, no conversion), boxes of 4 words x C
+// columns x 256 row pairs.  cuTensorMapEncodeTiled is a host-only driver call,
+// reached through the runtime's entry-point query so that the library needs no
+// link to libcuda.
 inline cudaError_t encode_field_map(CUtensorMap* map, const void* base, int n, int word_bytes, int cols) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void* p = nullptr;
@@ -115,11 +116,11 @@ inline cudaError_t encode_field_map(CUtensorMap* map, const void* base, int n, i
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }();
     if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)2 * n * word_bytes};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * cols), (cuuint32_t)kTmaBoxRows};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = fn(map, word_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+    const cuuint64_t dims[3] = {4, (cuuint64_t)n, (cuuint64_t)n / 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)4 * word_bytes, (cuuint64_t)4 * word_bytes * n};
+    const cuuint32_t box[3] = {4, (cuuint32_t)cols, (cuuint32_t)kTmaBoxRows};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult r = fn(map, word_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
                           const_cast<void*>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -227,16 +228,14 @@ template <typename T, int N> constexpr int col_mask() {
            (col_tma_ok<T, N, 8>() ? 256 : 0) | (col_tma_ok<T, N, 16>() ? 512 : 0);
 }
 
-// default column tile: the staged variant with 16-byte tile rows (two
-// complex64 or one complex128 column) where it exists -- the fastest or
-// within 2 % of the fastest tile at every size measured on GB300 --, else the
-// widest valid tile of at most 512 threads, unless its row segments are
-// shorter than one 32-byte sector, in which case the narrowest valid tile that
-// fills a sector (else the widest valid tile)
+// default column tile: the staged single-column tile where it exists (n >=
+// 512) -- the fastest or within 2 % of the fastest tile at every size
+// measured on GB300 --, else the widest valid tile of at most 512 threads,
+// unless its row segments are shorter than one 32-byte sector, in which case
+// the narrowest valid tile that fills a sector (else the widest valid tile)
 template <typename T, int N> constexpr int col_default() {
     constexpr int cs = 2 * (int)sizeof(T);
-    constexpr int staged = 16 / cs;  // columns per 16-byte tile row
-    if (col_tma_ok<T, N, staged>()) return kColTma | staged;
+    if (col_tma_ok<T, N, 1>()) return kColTma | 1;
     int best = 0;
     for (int i = 0; i < 5; ++i) {
         const int c = kColOptions[i];

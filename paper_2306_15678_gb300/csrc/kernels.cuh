@@ -320,6 +320,18 @@ template <typename T, int N, int LINES> __host__ __device__ constexpr int line_s
     return LINES > 1 ? base + (banks / LINES > 0 ? banks / LINES : 1) : pl;
 }
 
+// State layout (row-pair interleaved): element (y, x) of an n x n state array
+// lives at ((y / 2) n + x) 2 + (y mod 2).  The two rows of a pair alternate
+// element by element, so that a column is a sequence of pairs (y, y+1) of
+// adjacent complex values -- 16 bytes in complex64, the smallest unit a bulk
+// tensor copy moves -- and a single column can be staged by one such copy,
+// while a row is still read and written in one sweep of its row pair.  Only
+// the state between the passes uses this layout; the caller's fields are
+// row-major.
+template <int N> __host__ __device__ __forceinline__ size_t sidx(size_t y, size_t x) {
+    return ((y >> 1) * (size_t)N + x) * 2 + (y & 1);
+}
+
 // Global-memory access policies of the tile bodies: plain accesses for the
 // per-pass kernels, L2-only (.cg) accesses for the persistent batched kernel,
 // whose tiles are rewritten by other SMs within the same launch.
@@ -348,7 +360,7 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
     V* sm = smem + g * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = M::ld(src + row * N + j + m * TL);
+    for (int m = 0; m < E; ++m) v[m] = M::ld(src + sidx<N>(row, j + m * TL));
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         if (half == 0) conj_all(v);
@@ -370,7 +382,7 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
         }
     }
 #pragma unroll
-    for (int m = 0; m < E; ++m) M::st(dst + row * N + j + m * TL, v[m]);
+    for (int m = 0; m < E; ++m) M::st(dst + sidx<N>(row, j + m * TL), v[m]);
 }
 
 // Column pass body for C consecutive columns starting at col0 (thread layout:
@@ -393,7 +405,7 @@ __device__ __forceinline__ void col_tile(const typename vec2<T>::type* src, type
     V* sm = smem + c * LS;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = M::ld(src + (size_t)(j + m * TL) * N + col);
+    for (int m = 0; m < E; ++m) v[m] = M::ld(src + sidx<N>(j + m * TL, col));
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         if (half == 1) conj_all(v);  // second round: B_y = conj(F_y(conj(.)))
@@ -406,7 +418,7 @@ __device__ __forceinline__ void col_tile(const typename vec2<T>::type* src, type
     }
     conj_all(v);
 #pragma unroll
-    for (int m = 0; m < E; ++m) M::st(dst + (size_t)(j + m * TL) * N + col, v[m]);
+    for (int m = 0; m < E; ++m) M::st(dst + sidx<N>(j + m * TL, col), v[m]);
 }
 
 // Row pass kernel of the march; with DIAG the block also reduces sum |U|^2 and
@@ -437,11 +449,12 @@ k_col_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
     col_tile<T, N, C, MemPlain>(src, dst, tw, px, py, rot, blockIdx.x * C, reinterpret_cast<V*>(smraw));
 }
 
-// Forward row transform S = F_x U (load prologue); src may equal dst.
+// Forward row transform S = F_x U (load prologue): src row-major, dst in the
+// state layout (a different buffer).
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
                                   min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
-k_row_forward(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
+k_row_forward(const typename vec2<T>::type* __restrict__ src, typename vec2<T>::type* __restrict__ dst,
               const typename tab_of<T>::type* __restrict__ tw) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
@@ -455,11 +468,12 @@ k_row_forward(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
     for (int m = 0; m < E; ++m) v[m] = src[row * N + j + m * TL];
     fft_stockham<V, N, E, false>(v, smem + g * LS, tw, j);
 #pragma unroll
-    for (int m = 0; m < E; ++m) dst[row * N + j + m * TL] = v[m];
+    for (int m = 0; m < E; ++m) dst[sidx<N>(row, j + m * TL)] = v[m];
 }
 
-// Readout: U = B_x S / n per row; reduces sum/max |U|^2 into partials and
-// optionally writes U (field_out) and |U|^2 (flu_out).
+// Readout: U = B_x S / n per row (S in the state layout); reduces sum/max
+// |U|^2 into partials and optionally writes U (field_out) and |U|^2 (flu_out),
+// row-major.
 template <typename T, int N>
 __global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
                                   min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
@@ -475,7 +489,7 @@ k_readout(const typename vec2<T>::type* __restrict__ state, const typename tab_o
     const size_t row = (size_t)blockIdx.x * RPB + g;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = state[row * N + j + m * TL];
+    for (int m = 0; m < E; ++m) v[m] = state[sidx<N>(row, j + m * TL)];
     fft_stockham<V, N, E, true>(v, smem + g * LS, tw, j);
     const T inv = (T)1 / (T)N;
     T tsum = (T)0, tmax = (T)0;

@@ -69,15 +69,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (global_ns() - t0 > kTmaTimeoutNs) return false;
     return true;
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(src))
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
                  : "memory");
 }
 // commit the block's bulk stores and wait until they have read their source:
@@ -92,18 +94,21 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// The staged tile exists where a box row is a whole number of 16-byte units,
-// the column a whole number of boxes, and the stage fits in the transform
-// lines it aliases.
+// The staged tile exists where the column is a whole number of boxes (a box
+// holds kTmaBoxRows row pairs of the state layout, see sidx) and the stage fits
+// in the transform lines it aliases.  A box row -- the two values of a row pair
+// in each of the C columns -- is 16 C (complex64) or 32 C (complex128) bytes.
 template <typename T, int N, int C> __host__ __device__ constexpr bool col_tma_valid() {
-    return (int)sizeof(typename vec2<T>::type) * C % 16 == 0 && N % kTmaBoxRows == 0 &&
-           N <= line_stride<T, N, C>() && threads_per_line<T, N>() * C <= 1024 &&
+    return N % (2 * kTmaBoxRows) == 0 && N <= line_stride<T, N, C>() && threads_per_line<T, N>() * C <= 1024 &&
            line_stride<T, N, C>() * C * (int)sizeof(typename vec2<T>::type) + kTmaAlignPad <= 232448;
 }
 
 // Column pass with the tile staged by bulk tensor copies.  mload / mstore
-// describe src / dst as 2D arrays of n rows x 2n words (the real and imaginary
-// parts; the copies move bits).  Thread layout and arithmetic are col_tile's.
+// describe src / dst (state layout) as 3D arrays of n/2 row pairs x n columns x
+// 4 words (the real and imaginary parts of the pair's two values; the copies
+// move bits); a box holds kTmaBoxRows row pairs of C columns and lands in the
+// stage as [pair][column][2 values].  Thread layout and arithmetic are
+// col_tile's.
 // status may be null.  extra_tx (a test hook, 0 in use) makes block 0 expect
 // that many bytes more than its copies bring, so that its wait runs out.
 template <typename T, int N, int C>
@@ -114,7 +119,7 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
                int* __restrict__ status, uint32_t extra_tx) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>();
-    constexpr int LS = line_stride<T, N, C>(), BOXES = N / kTmaBoxRows;
+    constexpr int LS = line_stride<T, N, C>(), BOXES = N / (2 * kTmaBoxRows);
     constexpr uint32_t BYTES = (uint32_t)(N * C * sizeof(V));
     static_assert(col_tma_valid<T, N, C>(), "staged column tile");
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -122,15 +127,16 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     __shared__ int s_fail;
     const uint32_t pad = (kTmaAlign - (smem_u32(smraw) & (kTmaAlign - 1))) & (kTmaAlign - 1);
     V* smem = reinterpret_cast<V*>(smraw + pad);
-    V* stage = smem;  // [N][C], aliased by the transform lines once read
+    V* stage = smem;  // [N/2][C][2], aliased by the transform lines once read
     const int col0 = blockIdx.x * C;
-    const int x = 2 * col0;  // box origin in words: col0 * sizeof(V) is a multiple of 16 bytes
+    auto st = [](int y, int c) { return ((y >> 1) * C + c) * 2 + (y & 1); };  // stage index of (y, c)
     if (threadIdx.x == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, BYTES + (blockIdx.x == 0 ? extra_tx : 0u));
 #pragma unroll 1
-        for (int b = 0; b < BOXES; ++b) tma_load_2d(stage + b * kTmaBoxRows * C, &mload, x, b * kTmaBoxRows, &bar);
+        for (int b = 0; b < BOXES; ++b)
+            tma_load_3d(stage + b * kTmaBoxRows * C * 2, &mload, 0, col0, b * kTmaBoxRows, &bar);
         if (!mbar_wait_bounded(&bar, 0)) {
             if (status) atomicOr(status, 2);
             mbar_wait_bounded(&bar, 0);  // the copy still targets this block's memory
@@ -143,7 +149,7 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     const int col = col0 + c;
     V v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = stage[(j + m * TL) * C + c];
+    for (int m = 0; m < E; ++m) v[m] = stage[st(j + m * TL, c)];
     __syncthreads();  // the staged tile is consumed; the transforms reuse its memory
     V* sm = smem + c * LS;
 #pragma unroll 1
@@ -158,12 +164,13 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     }
     conj_all(v);
 #pragma unroll
-    for (int m = 0; m < E; ++m) stage[(j + m * TL) * C + c] = v[m];
+    for (int m = 0; m < E; ++m) stage[st(j + m * TL, c)] = v[m];
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll 1
-        for (int b = 0; b < BOXES; ++b) tma_store_2d(&mstore, x, b * kTmaBoxRows, stage + b * kTmaBoxRows * C);
+        for (int b = 0; b < BOXES; ++b)
+            tma_store_3d(&mstore, 0, col0, b * kTmaBoxRows, stage + b * kTmaBoxRows * C * 2);
         tma_store_commit_and_wait_read();
     }
 }
