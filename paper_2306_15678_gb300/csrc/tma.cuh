@@ -129,7 +129,8 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     V* smem = reinterpret_cast<V*>(smraw + pad);
     V* stage = smem;  // [N/2][C][2], aliased by the transform lines once read
     const int col0 = blockIdx.x * C;
-    auto st = [](int y, int c) { return ((y >> 1) * C + c) * 2 + (y & 1); };  // stage index of (y, c)
+    // stage index of (y, c): [y/2][c][y mod 2]
+    auto st = [](int y, int c) { return C == 1 ? y : ((y >> 1) * C + c) * 2 + (y & 1); };
     if (threadIdx.x == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
