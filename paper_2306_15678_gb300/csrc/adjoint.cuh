@@ -104,7 +104,7 @@ k_loss_seed(const typename vec2<T>::type* __restrict__ state, typename vec2<T>::
     constexpr int LS = line_stride<T, N, RPB>();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* smem = reinterpret_cast<V*>(smraw);
-    const int g = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
     const size_t row = (size_t)blockIdx.x * RPB + g;
     V* sm = smem + g * LS;
     V v[E];
@@ -141,7 +141,7 @@ k_adj_row(typename vec2<T>::type* __restrict__ gam, const typename vec2<T>::type
     constexpr int LS = line_stride<T, N, RPB>();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* smem = reinterpret_cast<V*>(smraw);
-    const int g = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
     const size_t row = (size_t)blockIdx.x * RPB + g;
     V* sm = smem + g * LS;
     V vt[E], gw[E];

@@ -332,6 +332,19 @@ template <int N> __host__ __device__ __forceinline__ size_t sidx(size_t y, size_
     return ((y >> 1) * (size_t)N + x) * 2 + (y & 1);
 }
 
+// Thread layout of the row-oriented kernels: RPB rows of TL threads each.
+// With an even number of rows, the two rows of each row pair alternate thread
+// by thread, so that the consecutive threads of a warp read and write
+// consecutive words of the interleaved row pair (see sidx).
+template <int TL, int RPB> __device__ __forceinline__ int row_of_thread() {
+    if constexpr (RPB % 2 == 0) return (int)(threadIdx.x & 1) + 2 * (int)(threadIdx.x / (2 * TL));
+    else return (int)(threadIdx.x / TL);
+}
+template <int TL, int RPB> __device__ __forceinline__ int lane_in_row() {
+    if constexpr (RPB % 2 == 0) return (int)(threadIdx.x % (2 * TL)) >> 1;
+    else return (int)(threadIdx.x % TL);
+}
+
 // Global-memory access policies of the tile bodies: plain accesses for the
 // per-pass kernels, L2-only (.cg) accesses for the persistent batched kernel,
 // whose tiles are rewritten by other SMs within the same launch.
@@ -355,7 +368,7 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>();
     constexpr int LS = line_stride<T, N, RPB>();
-    const int g = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
     const size_t row = (size_t)row0 + g;
     V* sm = smem + g * LS;
     V v[E];
@@ -461,7 +474,7 @@ k_row_forward(const typename vec2<T>::type* __restrict__ src, typename vec2<T>::
     constexpr int LS = line_stride<T, N, RPB>();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* smem = reinterpret_cast<V*>(smraw);
-    const int g = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
     const size_t row = (size_t)blockIdx.x * RPB + g;
     V v[E];
 #pragma unroll
@@ -485,7 +498,7 @@ k_readout(const typename vec2<T>::type* __restrict__ state, const typename tab_o
     constexpr int LS = line_stride<T, N, RPB>();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* smem = reinterpret_cast<V*>(smraw);
-    const int g = threadIdx.x / TL, j = threadIdx.x % TL;
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
     const size_t row = (size_t)blockIdx.x * RPB + g;
     V v[E];
 #pragma unroll
