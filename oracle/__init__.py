@@ -12,7 +12,8 @@ Every function here follows the passage named in the C source:
   step (Eq. 2), forward unnormalised, inverse 1/N per dimension.
 * ``propagator`` / ``linear`` -- diffraction, Lap_perp -> -k^2 (Eq. 1-2).
 * ``screen`` -- the pointwise Kerr / plasma / absorption screen (Eq. 2-3).
-* ``march`` -- Lie steps, diffraction then screen (Eq. 2).
+* ``march`` -- Lie steps, diffraction then screen (Eq. 2), or symmetric
+  Strang steps (half screen, diffraction, half screen).
 * ``power``, ``peak``, ``fluence``, ``loss`` -- readouts (w = UU*, Sec. 2-3).
 * ``adjoint`` -- reverse-mode gradient of the fluence loss (derived from the
   same steps; the paper has no adjoint).
@@ -91,6 +92,7 @@ def _configure(lib):
     lib.orc_loss.argtypes = [cp, cp, ctypes.c_int]
     lib.orc_loss.restype = ctypes.c_double
     lib.orc_march.argtypes = [P, cp, ctypes.c_int, cp, cp]
+    lib.orc_march_strang.argtypes = [P, cp, ctypes.c_int, cp, cp]
     lib.orc_adjoint.argtypes = [P, cp, cp, ctypes.c_int, ctypes.c_int, cp, cp]
     lib.orc_adjoint.restype = ctypes.c_double
     return lib
@@ -199,15 +201,21 @@ def loss(U, D) -> float:
     return float(_load().orc_loss(U.ctypes.data, D.ctypes.data, U.shape[0]))
 
 
-def march(U0, cfg: dict, nsteps: int, record: bool = True):
-    """March U0 by nsteps Lie steps.  Returns (U, power[nsteps+1], peak[nsteps+1])."""
+def march(U0, cfg: dict, nsteps: int, record: bool = True, scheme: str | None = None):
+    """March U0 by nsteps Lie steps (diffraction, then screen), or Strang steps
+    (half screen, diffraction, half screen) when scheme -- or cfg["scheme"] --
+    is "strang".  Returns (U, power[nsteps+1], peak[nsteps+1])."""
     U = _c128(U0).copy()
     p = params(cfg)
     pw = np.zeros(nsteps + 1) if record else None
     pk = np.zeros(nsteps + 1) if record else None
-    _load().orc_march(ctypes.byref(p), U.ctypes.data, int(nsteps),
-                      pw.ctypes.data if record else None,
-                      pk.ctypes.data if record else None)
+    scheme = scheme or cfg.get("scheme", "lie")
+    if scheme not in ("lie", "strang"):
+        raise ValueError(f"scheme {scheme!r}")
+    fn = _load().orc_march_strang if scheme == "strang" else _load().orc_march
+    fn(ctypes.byref(p), U.ctypes.data, int(nsteps),
+       pw.ctypes.data if record else None,
+       pk.ctypes.data if record else None)
     return U, pw, pk
 
 

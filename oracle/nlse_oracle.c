@@ -348,6 +348,24 @@ void orc_march(const orc_params *p, cplx *U, int nsteps, double *power, double *
     }
 }
 
+/* nsteps symmetric (Strang) steps in place: half a screen step, the full
+ * diffraction step, half a screen step (the phase-screen operator exponential
+ * of Eq. 2 split symmetrically; each half-screen is the frozen-intensity
+ * screen of orc_screen over dz/2).  power[k], peak[k] after k steps. */
+void orc_march_strang(const orc_params *p, cplx *U, int nsteps, double *power, double *peak) {
+    orc_params half = *p;
+    half.dz = 0.5 * p->dz;
+    if (power) power[0] = orc_power(U, p->n, p->L);
+    if (peak) peak[0] = orc_peak(U, p->n);
+    for (int s = 0; s < nsteps; ++s) {
+        orc_screen(&half, U);
+        orc_linear(p, U);
+        orc_screen(&half, U);
+        if (power) power[s + 1] = orc_power(U, p->n, p->L);
+        if (peak) peak[s + 1] = orc_peak(U, p->n);
+    }
+}
+
 /* -------------------------------------------------------------- adjoint -- */
 
 /* Reverse-mode derivative of J(theta, U0) = loss(march(U0, nsteps), D).

@@ -227,6 +227,39 @@ def test_time_reversal_recovers_input():
     assert rel_l2(U, U0) < 1e-11
 
 
+def strang_case(M, Z=10.0, terms=configs.KERR | configs.DIFFRACTION):
+    cfg = configs.physics(64, 0.64, Z / M, terms)
+    cfg["beam"] = dict(w0=0.05, P=10.0 * configs.critical_power(), amp=0.05, ell_cells=3.0, seed=3,
+                       phase=0.0, phase_seed=None)
+    return cfg
+
+
+def test_strang_is_second_order_and_lie_first_order():
+    """Symmetric splitting of the step (Eq. 2: half screen, diffraction, half
+    screen) has a global error O(dz^2), the Lie step O(dz): halving dz over a
+    fixed 10 cm divides the error by ~4 and ~2 (Kerr + diffraction, the peak
+    doubles over the distance)."""
+    U0 = beams.make_field(strang_case(1))
+    ref, _, _ = oracle.march(U0, strang_case(640), 640, scheme="strang")
+    for scheme, ratio in (("strang", 4.0), ("lie", 2.0)):
+        err = [rel_l2(oracle.march(U0, strang_case(M), M, scheme=scheme)[0], ref) for M in (10, 20, 40)]
+        for a, b in zip(err, err[1:]):
+            assert abs(a / b / ratio - 1) < 0.1, (scheme, err)
+    assert rel_l2(oracle.march(U0, strang_case(10), 10, scheme="strang")[0], ref) < \
+        0.2 * rel_l2(oracle.march(U0, strang_case(10), 10, scheme="lie")[0], ref)
+
+
+def test_strang_step_is_time_symmetric():
+    """Lossless symmetric step: S(-dz) S(dz) is the identity (the half screens
+    keep |U| and the diffraction step is unitary), to rounding."""
+    cfg = strang_case(30, terms=configs.KERR | configs.PLASMA | configs.DIFFRACTION)
+    U0 = beams.make_field(cfg)
+    U, _, _ = oracle.march(U0, cfg, 30, scheme="strang")
+    back, _, _ = oracle.march(U, dict(cfg, dz=-cfg["dz"]), 30, scheme="strang")
+    assert rel_l2(U, U0) > 1e-3
+    assert rel_l2(back, U0) < 1e-11
+
+
 def test_mpa_discrete_energy_balance():
     """With absorption the power after a step is sum I_v exp(-beta I_v^(K-1) dz) dx^2
     where v is the diffracted field (the linear step is unitary)."""
@@ -413,6 +446,7 @@ MUTANTS = [
      "for (int r = 0; r < n; ++r) col[r] = a[(size_t)c * n + r];", "fft"),
     ("adjoint screen conj dropped", "G[i] = conj(e) * gw + 2.0",
      "G[i] = e * gw + 2.0", "adjoint"),
+    ("Strang half screen over the full step", "half.dz = 0.5 * p->dz;", "half.dz = p->dz;", "strang"),
 ]
 
 
@@ -428,6 +462,7 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "mpa": test_mpa_screen_exact_attenuation,
         "fft": lambda: test_fft2_matches_brute_force_dft(8),
         "adjoint": test_adjoint_field_gradient_matches_directional_difference,
+        "strang": test_strang_is_second_order_and_lie_first_order,
     }
     with pytest.raises(AssertionError):
         pins[pin]()
