@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-strang", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--large-adjoint-steps", type=int, default=100)
     return ap.parse_args()
@@ -430,6 +431,27 @@ def main():
                     "step_hbm_frac": (2 * bytes_launch) / (ms / args.steps / 1e3) / 1e9 / peak_gbs,
                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_note}
 
+        # ---- symmetric (Strang) steps on the same field: one more screen per row pass
+        strang = None
+        if not args.no_strang:
+            gs = Grid(dict(cfg, scheme="strang"), precision="fp32", diag_every=1, device=dev, stream=stream)
+            capi.nlse_set_column_tile(gs.h, cols)
+            gs.load(U0)
+            gs.step(3)
+            ks = max(50, min(args.steps // 4, 500))
+            torch.cuda.synchronize(dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            gs.step(ks)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            mss = a0.elapsed_time(a1)
+            strang = {"value": n * n * ks / (mss / 1e3), "unit": UNIT, "steps": ks,
+                      "ms_per_step": mss / ks, "over_lie_time": (mss / ks) / (ms / args.steps),
+                      "note": "global error O(dz^2) instead of O(dz): one call opens and closes its half screens"}
+            gs.close()
+
         # ---- FP64 march on the same field (precision comparison)
         fp64 = None
         if not args.no_fp64:
@@ -487,7 +509,7 @@ def main():
             "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
-            "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
+            "strang": strang, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

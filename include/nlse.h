@@ -96,8 +96,14 @@ typedef struct nlse_params {
     double betaK;         /* K-photon absorption coefficient, cm^(2K-3) W^(1-K) */
     double theta[6];      /* complex screen gains (re, im) for Kerr, plasma, absorption */
     int32_t diag_every;   /* record power and peak every this many steps (0 = never) */
-    int32_t reserved;     /* must be 0 */
+    int32_t scheme;       /* NLSE_LIE or NLSE_STRANG (see nlse_step) */
 } nlse_params;
+
+/* Splitting of a step (Eq. 2): NLSE_LIE -- diffraction over dz, then the screen
+ * over dz; NLSE_STRANG -- the screen over dz/2, diffraction over dz, the screen
+ * over dz/2 (symmetric, second order in dz).  The batched march and the
+ * adjoint take NLSE_LIE only. */
+enum { NLSE_LIE = 0, NLSE_STRANG = 1 };
 
 typedef struct nlse_grid nlse_grid;
 

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libnlse.so")
 NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
 NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
 NLSE_COL_TMA = 0x100  # column tile staged with bulk tensor copies (or'ed with the width)
+NLSE_LIE, NLSE_STRANG = 0, 1  # splitting of a step
 NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15
 NLSE_FP64, NLSE_FP32 = 0, 1
 
@@ -37,7 +38,7 @@ class nlse_params(ctypes.Structure):
         ("betaK", ctypes.c_double),
         ("theta", ctypes.c_double * 6),
         ("diag_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
     ]
 
 

@@ -263,7 +263,7 @@ nlse_status bvalidate(int count, const nlse_params* ps) {
         size_t bytes;
         nlse_status st = nlse_workspace_size(&ps[b], &bytes);
         if (st != NLSE_OK) return st;
-        if (ps[b].precision != NLSE_FP32) return NLSE_EUNSUPPORTED;
+        if (ps[b].precision != NLSE_FP32 || ps[b].scheme != NLSE_LIE) return NLSE_EUNSUPPORTED;
         const int k = ilog2i(ps[b].n);
         if (k < kBatchMinLog2 || k > kBatchMaxLog2) return NLSE_EUNSUPPORTED;
     }

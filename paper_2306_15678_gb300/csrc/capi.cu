@@ -82,7 +82,7 @@ nlse_status validate(const nlse_params* p) {
     if ((p->terms & NLSE_PLASMA) && !(p->rho_c > 0.0)) return NLSE_EINVAL;
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(p->theta[i])) return NLSE_EINVAL;
-    if (p->diag_every < 0 || p->reserved != 0) return NLSE_EINVAL;
+    if (p->diag_every < 0 || (p->scheme != NLSE_LIE && p->scheme != NLSE_STRANG)) return NLSE_EINVAL;
     return NLSE_OK;
 }
 
@@ -169,6 +169,8 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     c.K = p->K;
     c.active = (p->terms & (NLSE_KERR | NLSE_PLASMA | NLSE_MPA)) ? 1 : 0;
     c.has_gain = (c.re_k != (T)0 || c.re_p != (T)0 || c.re_a != (T)0) ? 1 : 0;
+    c.reps = 1;
+    c.scale = (T)1;
     return c;
 }
 
@@ -346,15 +348,31 @@ nlse_status flush_diag_any(nlse_grid* g) {
     return g->p.precision == NLSE_FP64 ? flush_diag<double>(g) : flush_diag<float>(g);
 }
 
+// The march.  Lie: per step the column pass (diffraction) and the row pass
+// (screen).  Strang: the screen coefficients are those of dz/2; a row pass
+// with the screen alone opens the call (the first half screen), every step's
+// row pass then applies its closing half screen, records the diagnostics and,
+// except in the last step of the call, applies the opening half screen of the
+// next step; so a call of m steps costs m + 1 row-pass sweeps and the state
+// between calls is the field at a whole step, as in the Lie march.
 template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_t* ev = nullptr) {
     const KernelSet<T>* ks = Sel<T>::ks(g);
     VT<T>* field = at<T>(g, g->lay.state);
     const int n = g->p.n;
     double* partials = dat(g, g->lay.partials);
-    const double dx = g->p.L / g->p.n;
+    const bool strang = g->p.scheme == NLSE_STRANG;
+    ScreenCoef<T> sc = Sel<T>::sc(g);
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
         const int64_t k = g->steps;
+        if (strang && s == 0) {  // the opening half screen of the call: B_x S / n, screen, F_x
+            sc.reps = 1;
+            sc.scale = (T)1 / (T)n;
+            if (ks->row_pass(field, field, twiddles_at<T>(g->ws + g->lay.tw, n, k), sc, partials, false,
+                             g->stream) != cudaSuccess)
+                return NLSE_ECUDA;
+            sc.scale = (T)1;
+        }
         const WT<T>* tw = twiddles_at<T>(g->ws + g->lay.tw, n, k);
         const WT<T>* px = table_at<T>(g->ws + g->lay.px, n, k);
         const WT<T>* py = table_at<T>(g->ws + g->lay.py, n, k);
@@ -369,7 +387,8 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
         // a diagnostic step leaves its per-block partials in the next slot of the
         // diag buffer; a full buffer is finalised into the history in one launch
         double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * ks->row_blocks;
-        e = ks->row_pass(field, field, tw, Sel<T>::sc(g), diag ? slot : partials, diag, g->stream);
+        sc.reps = strang && s + 1 < nsteps ? 2 : 1;
+        e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (diag && ++g->diag_pending == kDiagBatch && flush_diag<T>(g) != NLSE_OK) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -513,14 +532,16 @@ nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_works
     g->lay = lay;
     const int k = log2_exact(p->n);
     if (cudaGetDevice(&g->device) != cudaSuccess) { delete g; return NLSE_ECUDA; }
+    nlse_params screen_p = *p;  // the screen of one Lie step, or half of a symmetric step
+    if (p->scheme == NLSE_STRANG) screen_p.dz = 0.5 * p->dz;
     if (p->precision == NLSE_FP64) {
         g->k64 = kernels_f64(k);
         g->cols = g->k64->col_default;
-        g->sc64 = screen_coef<double>(p);
+        g->sc64 = screen_coef<double>(&screen_p);
     } else {
         g->k32 = kernels_f32(k);
         g->cols = g->k32->col_default;
-        g->sc32 = screen_coef<float>(p);
+        g->sc32 = screen_coef<float>(&screen_p);
     }
     if (const char* env = std::getenv("NLSE_DEBUG_COL_EXTRA_TX")) g->debug_extra_tx = (unsigned)std::atoi(env);
     if (const char* env = std::getenv("NLSE_COL_TILE")) {
@@ -964,6 +985,7 @@ nlse_status nlse_adjoint_workspace_size(const nlse_params* p, int32_t nsteps, in
     if (!bytes || nsteps < 1 || ckpt_every < 1) return NLSE_EINVAL;
     nlse_status st = validate(p);
     if (st != NLSE_OK) return st;
+    if (p->scheme != NLSE_LIE) return NLSE_EUNSUPPORTED;  // the adjoint differentiates the Lie march
     *bytes = adj_layout_for(p->n, p->precision, nsteps, std::min(ckpt_every, nsteps)).total;
     return NLSE_OK;
 }
@@ -974,6 +996,7 @@ nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ck
     *out = nullptr;
     nlse_status st = validate(p);
     if (st != NLSE_OK) return st;
+    if (p->scheme != NLSE_LIE) return NLSE_EUNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(dev_workspace) & 255) return NLSE_EINVAL;
     const int ck = std::min(ckpt_every, nsteps);
     AdjLayout lay = adj_layout_for(p->n, p->precision, nsteps, ck);

@@ -25,6 +25,12 @@ template <typename T> struct ScreenCoef {
     int K;         // multiphoton order
     int active;    // 0: no nonlinear term (screen is the identity)
     int has_gain;  // 0: Re s = 0 everywhere (pure phase screen)
+    int reps;      // screens the row pass applies in a row (2: the two half
+                   // screens that meet between symmetric steps), power and peak
+                   // taken after the first
+    T scale;       // factor on the field entering the screen: 1, or 1/n for a
+                   // row pass not preceded by a column pass (whose tables carry
+                   // the 1/n^2 of the inverse transforms); a power of two, exact
 };
 
 template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
@@ -380,16 +386,23 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
         fft_stockham<V, N, E, false>(v, sm, tw, j);
         if (half == 0) {
             conj_all(v);  // v = B_x S: the field entering the screen
-            if (sc.active) {
+            if (sc.scale != (T)1) {  // (uniform)
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc);
+                for (int m = 0; m < E; ++m) v[m] = cscale(v[m], sc.scale);
             }
-            if constexpr (DIAG) {
+#pragma unroll 1
+            for (int rep = 0; rep < sc.reps; ++rep) {
+                if (sc.active) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const T a = v[m].x * v[m].x + v[m].y * v[m].y;
-                    tsum += a;
-                    tmax = fmax(tmax, a);
+                    for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc);
+                }
+                if (DIAG && rep == 0) {
+#pragma unroll
+                    for (int m = 0; m < E; ++m) {
+                        const T a = v[m].x * v[m].x + v[m].y * v[m].y;
+                        tsum += a;
+                        tmax = fmax(tmax, a);
+                    }
                 }
             }
         }

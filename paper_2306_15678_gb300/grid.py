@@ -11,6 +11,7 @@ import torch
 from . import capi
 
 _PREC = {"fp64": capi.NLSE_FP64, "fp32": capi.NLSE_FP32}
+_SCHEME = {"lie": capi.NLSE_LIE, "strang": capi.NLSE_STRANG}
 
 
 def make_params(cfg: dict, precision: str | None = None, diag_every: int = 0) -> capi.nlse_params:
@@ -26,7 +27,10 @@ def make_params(cfg: dict, precision: str | None = None, diag_every: int = 0) ->
     for i in range(6):
         p.theta[i] = float(th[i])
     p.diag_every = int(diag_every)
-    p.reserved = 0
+    scheme = cfg.get("scheme", "lie")
+    if scheme not in _SCHEME:
+        raise ValueError(f"scheme {scheme!r}: expected 'lie' or 'strang'")
+    p.scheme = _SCHEME[scheme]
     return p
 
 

@@ -46,7 +46,7 @@ def test_workspace_size_and_validation_on_host():
            ("n", 4, capi.NLSE_EUNSUPPORTED), ("precision", 7, capi.NLSE_EUNSUPPORTED),
            ("K", 0, capi.NLSE_EINVAL), ("terms", 16, capi.NLSE_EINVAL),
            ("L", -1.0, capi.NLSE_EINVAL), ("dz", 0.0, capi.NLSE_EINVAL),
-           ("diag_every", -1, capi.NLSE_EINVAL), ("reserved", 1, capi.NLSE_EINVAL)]
+           ("diag_every", -1, capi.NLSE_EINVAL), ("scheme", 2, capi.NLSE_EINVAL)]
     for field, val, code in bad:
         q = make_params(cfg)
         setattr(q, field, val)
@@ -84,3 +84,20 @@ def test_large_adjoint_fits_with_sqrt_checkpointing():
     assert (k + nck) * field <= ws <= (k + nck + 6) * field
     assert ws < 60 * 2 ** 30
     assert capi.nlse_adjoint_workspace_size(p, M, M) > 25 * ws
+
+
+def test_symmetric_steps_only_for_single_grids():
+    """The batched march and the adjoint take Lie steps only: asking either for
+    the symmetric scheme is NLSE_EUNSUPPORTED, on the host, before any launch."""
+    cfg = dict(configs.scaled(configs.cfg_dense_fp32(), 512), scheme="strang")
+    p = make_params(cfg)
+    assert p.scheme == capi.NLSE_STRANG
+    assert capi.nlse_workspace_size(p) > 0
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_adjoint_workspace_size(p, 10, 5)
+    assert ei.value.status == capi.NLSE_EUNSUPPORTED
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_batch_workspace_size([p])
+    assert ei.value.status == capi.NLSE_EUNSUPPORTED
+    with pytest.raises(ValueError):
+        make_params(dict(cfg, scheme="leapfrog"))
