@@ -48,9 +48,10 @@ __device__ __forceinline__ void screen_factor_and_slope(T u, const AdjCoef<T>& a
     *uk = k;
     *uk1 = k1;
     if constexpr (sizeof(T) == 4) {
-        const float em1 = c.has_gain ? expm1_(re) : 0.0f;
+        const unsigned warp = (blockDim.x & 31) == 0 ? 0xffffffffu : __activemask();
+        const float em1 = c.has_gain ? expm1_(re, warp) : 0.0f;
         float sn, cm1;
-        sin_cosm1(im, &sn, &cm1);
+        sin_cosm1(im, &sn, &cm1, warp);
         *er = 1.0f + fmaf(em1, cm1, em1 + cm1);
         *ei = fmaf(em1, sn, sn);
     } else {

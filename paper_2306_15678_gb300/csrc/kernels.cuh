@@ -54,8 +54,9 @@ template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
 // the warp has |x| <= pi/4 (per-step screen phases usually are) the reduction
 // and the quadrant fix-up are skipped: they would leave x unchanged, so the
 // results are the same bits either way.
-__device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
-    const bool small = __all_sync(__activemask(), fabsf(x) <= 0.7853982f);  // uniform per warp
+// warp: the lanes taking part (all 32 in blocks of whole warps).
+__device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1, unsigned warp = 0xffffffffu) {
+    const bool small = __all_sync(warp, fabsf(x) <= 0.7853982f);  // uniform per warp
     float r = x, q = 0.0f;
     if (!small) {
         q = rintf(x * 0.636619772367581343f);           // x / (pi/2)
@@ -89,13 +90,13 @@ __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1) {
 
 // exp(x) - 1: Taylor polynomial to x^5 for |x| < 1/16 (error < 3e-11 relative),
 // expf(x) - 1 beyond; expf is skipped when no lane of the warp needs it
-__device__ __forceinline__ float expm1_(float x) {
+__device__ __forceinline__ float expm1_(float x, unsigned warp = 0xffffffffu) {
     float p = fmaf(x, 8.33333333333333333e-3f, 4.16666666666666667e-2f);
     p = fmaf(x, p, 1.66666666666666667e-1f);
     p = fmaf(x, p, 0.5f);
     const float small = fmaf(x * x, p, x);
     const bool in_range = fabsf(x) < 0.0625f;
-    if (__all_sync(__activemask(), in_range)) return small;
+    if (__all_sync(warp, in_range)) return small;
     return in_range ? small : expf(x) - 1.0f;
 }
 
@@ -117,13 +118,13 @@ template <typename T> __device__ __forceinline__ void screen_exponent(T u, const
 
 // FP32: U = v + v d with d = exp(re + i im) - 1 = expm1(re) e^{i im} + (e^{i im} - 1),
 // so that the per-step change, not the field, carries the rounding of the factor
-__device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>& c) {
+__device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>& c, unsigned warp) {
     const float u = (v.x * v.x + v.y * v.y) * c.inv_iref;
     float re, im;
     screen_exponent(u, c, &re, &im);
-    const float em1 = c.has_gain ? expm1_(re) : 0.0f;  // uniform: pure phase screens skip it
+    const float em1 = c.has_gain ? expm1_(re, warp) : 0.0f;  // uniform: pure phase screens skip it
     float sn, cm1;
-    sin_cosm1(im, &sn, &cm1);
+    sin_cosm1(im, &sn, &cm1, warp);
     const float dre = fmaf(em1, cm1, em1 + cm1);  // (1 + em1)(1 + cm1) - 1
     const float dim = fmaf(em1, sn, sn);          // (1 + em1) sin
     // the whole change v d first (accurate relative to itself), then a single
@@ -138,7 +139,7 @@ __device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>
 }
 
 // FP64: the factor exp(re) (cos im + i sin im) directly
-__device__ __forceinline__ double2 apply_screen(double2 v, const ScreenCoef<double>& c) {
+__device__ __forceinline__ double2 apply_screen(double2 v, const ScreenCoef<double>& c, unsigned) {
     const double u = (v.x * v.x + v.y * v.y) * c.inv_iref;
     double re, im;
     screen_exponent(u, c, &re, &im);
@@ -390,11 +391,13 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[m] = cscale(v[m], sc.scale);
             }
+            // lanes of this warp (blocks of fewer than 32 threads exist for tiny grids)
+            const unsigned warp = (blockDim.x & 31) == 0 ? 0xffffffffu : __activemask();
 #pragma unroll 1
             for (int rep = 0; rep < sc.reps; ++rep) {
                 if (sc.active) {
 #pragma unroll
-                    for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc);
+                    for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc, warp);
                 }
                 if (DIAG && rep == 0) {
 #pragma unroll
