@@ -54,6 +54,19 @@ template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
 // the warp has |x| <= pi/4 (per-step screen phases usually are) the reduction
 // and the quadrant fix-up are skipped: they would leave x unchanged, so the
 // results are the same bits either way.
+// sin r and cos r - 1 for |r| <= pi/4 (the polynomials above)
+__device__ __forceinline__ void sin_cosm1_core(float r, float* sr, float* cr1) {
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573192239858906e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(r2, ps, 8.33333333333333333e-3f);
+    ps = fmaf(r2, ps, -1.66666666666666667e-1f);
+    *sr = fmaf(r * r2, ps, r);                           // sin r
+    float pc = fmaf(r2, -2.75573192239858906e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(r2, pc, -1.38888888888888889e-3f);
+    pc = fmaf(r2, pc, 4.16666666666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    *cr1 = r2 * pc;                                      // cos r - 1
+}
 // warp: the lanes taking part (all 32 in blocks of whole warps).
 __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1, unsigned warp = 0xffffffffu) {
     const bool small = __all_sync(warp, fabsf(x) <= 0.7853982f);  // uniform per warp
@@ -64,16 +77,8 @@ __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1, unsigne
         r = fmaf(-q, -4.37113900018624283e-8f, r);       // pi/2 - fl32(pi/2)
         r = fminf(fmaxf(r, -0.7853982f), 0.7853982f);
     }
-    const float r2 = r * r;
-    float ps = fmaf(r2, 2.75573192239858906e-6f, -1.98412698412698413e-4f);
-    ps = fmaf(r2, ps, 8.33333333333333333e-3f);
-    ps = fmaf(r2, ps, -1.66666666666666667e-1f);
-    const float sr = fmaf(r * r2, ps, r);                // sin r
-    float pc = fmaf(r2, -2.75573192239858906e-7f, 2.48015873015873016e-5f);
-    pc = fmaf(r2, pc, -1.38888888888888889e-3f);
-    pc = fmaf(r2, pc, 4.16666666666666667e-2f);
-    pc = fmaf(r2, pc, -0.5f);
-    const float cr1 = r2 * pc;                           // cos r - 1
+    float sr, cr1;
+    sin_cosm1_core(r, &sr, &cr1);
     if (small) {
         *s = sr;
         *cm1 = cr1;
@@ -90,11 +95,14 @@ __device__ __forceinline__ void sin_cosm1(float x, float* s, float* cm1, unsigne
 
 // exp(x) - 1: Taylor polynomial to x^5 for |x| < 1/16 (error < 3e-11 relative),
 // expf(x) - 1 beyond; expf is skipped when no lane of the warp needs it
-__device__ __forceinline__ float expm1_(float x, unsigned warp = 0xffffffffu) {
+__device__ __forceinline__ float expm1_core(float x) {  // |x| < 1/16
     float p = fmaf(x, 8.33333333333333333e-3f, 4.16666666666666667e-2f);
     p = fmaf(x, p, 1.66666666666666667e-1f);
     p = fmaf(x, p, 0.5f);
-    const float small = fmaf(x * x, p, x);
+    return fmaf(x * x, p, x);
+}
+__device__ __forceinline__ float expm1_(float x, unsigned warp = 0xffffffffu) {
+    const float small = expm1_core(x);
     const bool in_range = fabsf(x) < 0.0625f;
     if (__all_sync(warp, in_range)) return small;
     return in_range ? small : expf(x) - 1.0f;
@@ -122,9 +130,16 @@ __device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>
     const float u = (v.x * v.x + v.y * v.y) * c.inv_iref;
     float re, im;
     screen_exponent(u, c, &re, &im);
-    const float em1 = c.has_gain ? expm1_(re, warp) : 0.0f;  // uniform: pure phase screens skip it
-    float sn, cm1;
-    sin_cosm1(im, &sn, &cm1, warp);
+    // one vote for both fast paths: the usual case, every lane's phase within
+    // pi/4 and gain below 1/16 (the same bits as the general paths give)
+    float em1, sn, cm1;
+    if (__all_sync(warp, fabsf(im) <= 0.7853982f && fabsf(re) < 0.0625f)) {
+        em1 = c.has_gain ? expm1_core(re) : 0.0f;  // uniform: pure phase screens skip it
+        sin_cosm1_core(im, &sn, &cm1);
+    } else {
+        em1 = c.has_gain ? expm1_(re, warp) : 0.0f;
+        sin_cosm1(im, &sn, &cm1, warp);
+    }
     const float dre = fmaf(em1, cm1, em1 + cm1);  // (1 + em1)(1 + cm1) - 1
     const float dim = fmaf(em1, sn, sn);          // (1 + em1) sin
     // the whole change v d first (accurate relative to itself), then a single
