@@ -15,6 +15,7 @@ Every function here follows the passage named in the C source:
 * ``march`` -- Lie steps, diffraction then screen (Eq. 2), or symmetric
   Strang steps (half screen, diffraction, half screen).
 * ``power``, ``peak``, ``fluence``, ``loss`` -- readouts (w = UU*, Sec. 2-3).
+* ``hot_areas`` -- number of closed regions with w >= w_p (Sec. 3.3).
 * ``adjoint`` -- reverse-mode gradient of the fluence loss (derived from the
   same steps; the paper has no adjoint).
 
@@ -93,6 +94,8 @@ def _configure(lib):
     lib.orc_loss.restype = ctypes.c_double
     lib.orc_march.argtypes = [P, cp, ctypes.c_int, cp, cp]
     lib.orc_march_strang.argtypes = [P, cp, ctypes.c_int, cp, cp]
+    lib.orc_hot_areas.argtypes = [cp, ctypes.c_int, ctypes.c_double, ctypes.c_int, cp]
+    lib.orc_hot_areas.restype = ctypes.c_int
     lib.orc_adjoint.argtypes = [P, cp, cp, ctypes.c_int, ctypes.c_int, cp, cp]
     lib.orc_adjoint.restype = ctypes.c_double
     return lib
@@ -217,6 +220,18 @@ def march(U0, cfg: dict, nsteps: int, record: bool = True, scheme: str | None = 
        pw.ctypes.data if record else None,
        pk.ctypes.data if record else None)
     return U, pw, pk
+
+
+def hot_areas(w, wp: float, conn: int = 4):
+    """Number of connected regions where w >= wp (Sec. 3.3 "hot areas"), and the
+    labels: -1 outside, else the smallest row-major index of the region."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = w.shape[0]
+    labels = np.empty((n, n), dtype=np.int32)
+    count = _load().orc_hot_areas(w.ctypes.data, n, float(wp), int(conn), labels.ctypes.data)
+    if count < 0:
+        raise ValueError("hot_areas: bad argument")
+    return int(count), labels
 
 
 def adjoint(U0, D, cfg: dict, nsteps: int, ckpt: int = 20):

@@ -366,6 +366,53 @@ void orc_march_strang(const orc_params *p, cplx *U, int nsteps, double *power, d
     }
 }
 
+/* ------------------------------------------------------------ hot areas -- */
+
+/* "Hot areas" (Sec. 3.3): the closed regions of the beam cross-section where the
+ * fluence w >= w_p, counted as the connected components of the thresholded
+ * grid.  conn = 4 (edge neighbours) or 8 (edge and corner neighbours); the
+ * window is not periodic.  labels[i] = -1 outside the regions, else the
+ * smallest row-major index of the pixel's region (row-major scan order makes
+ * the first pixel met the smallest).  Returns the number of regions, or -1 for
+ * a bad argument.  Plain flood fill with an explicit stack. */
+int orc_hot_areas(const double *w, int n, double wp, int conn, int32_t *labels) {
+    if (n < 1 || (conn != 4 && conn != 8)) return -1;
+    size_t nn = (size_t)n * n;
+    for (size_t i = 0; i < nn; ++i) labels[i] = -2;  /* -2: unvisited */
+    size_t *stack = malloc(nn * sizeof(size_t));
+    if (!stack) return -1;
+    int count = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        if (labels[i] != -2) continue;
+        if (!(w[i] >= wp)) { labels[i] = -1; continue; }
+        ++count;
+        size_t top = 0;
+        stack[top++] = i;
+        labels[i] = (int32_t)i;
+        while (top > 0) {
+            size_t q = stack[--top];
+            int r = (int)(q / (size_t)n), c = (int)(q % (size_t)n);
+            for (int dr = -1; dr <= 1; ++dr)
+                for (int dc = -1; dc <= 1; ++dc) {
+                    if (dr == 0 && dc == 0) continue;
+                    if (conn == 4 && dr != 0 && dc != 0) continue;
+                    int rr = r + dr, cc = c + dc;
+                    if (rr < 0 || rr >= n || cc < 0 || cc >= n) continue;
+                    size_t t = (size_t)rr * n + cc;
+                    if (labels[t] != -2) continue;
+                    if (w[t] >= wp) {
+                        labels[t] = (int32_t)i;
+                        stack[top++] = t;
+                    } else {
+                        labels[t] = -1;
+                    }
+                }
+        }
+    }
+    free(stack);
+    return count;
+}
+
 /* -------------------------------------------------------------- adjoint -- */
 
 /* Reverse-mode derivative of J(theta, U0) = loss(march(U0, nsteps), D).

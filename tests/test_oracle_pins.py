@@ -429,6 +429,53 @@ def test_input_generator_power_and_noise_statistics():
     assert c > 0.8
 
 
+# ------------------------------------------------ hot areas (Sec. 3.3)
+
+def test_hot_areas_hand_made_patterns():
+    """Closed regions with w >= w_p, counted by hand: none, one, a ring (one
+    region around a hole), a 4-connected chain, diagonal touching (two regions
+    with edge neighbours, one with corner neighbours), a checkerboard."""
+    z = np.zeros((8, 8))
+    assert oracle.hot_areas(z, 0.5)[0] == 0
+    assert oracle.hot_areas(z + 1, 0.5)[0] == 1
+    ring = np.zeros((8, 8)); ring[1:6, 1:6] = 1; ring[2:5, 2:5] = 0
+    assert oracle.hot_areas(ring, 0.5, 4)[0] == 1
+    diag = np.zeros((8, 8)); diag[1, 1] = diag[2, 2] = 1
+    assert oracle.hot_areas(diag, 0.5, 4)[0] == 2
+    assert oracle.hot_areas(diag, 0.5, 8)[0] == 1
+    board = np.indices((8, 8)).sum(axis=0) % 2 == 0
+    assert oracle.hot_areas(board.astype(float), 0.5, 4)[0] == 32
+    assert oracle.hot_areas(board.astype(float), 0.5, 8)[0] == 1
+    edge = np.zeros((8, 8)); edge[0, :] = 1; edge[7, :] = 1  # not joined across the window edge
+    assert oracle.hot_areas(edge, 0.5)[0] == 2
+    w = np.array([[1.0, 0.999999], [0.0, 2.0]])
+    assert oracle.hot_areas(w, 1.0, 4)[0] == 2      # w >= w_p, the threshold value included
+    _, lab = oracle.hot_areas(w, 1.0, 4)
+    assert lab.tolist() == [[0, -1], [-1, 3]]
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("density", [0.3, 0.55, 0.6, 0.8])
+def test_hot_areas_match_library_labelling(conn, density):
+    """Random masks near and away from the percolation threshold: the count and
+    the partition agree with scipy.ndimage.label (a library routine), and each
+    label is the smallest index of its region."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(int(density * 100) + conn)
+    w = rng.random((96, 96))
+    mask = w >= 1 - density
+    structure = np.ones((3, 3)) if conn == 8 else None
+    ref, nref = ndimage.label(mask, structure=structure)
+    count, lab = oracle.hot_areas(w, 1 - density, conn)
+    assert count == nref
+    assert np.array_equal(lab >= 0, mask)
+    pairs = set(zip(lab[mask].tolist(), ref[mask].tolist()))
+    assert len(pairs) == nref  # one-to-one between the two labellings
+    idx = np.arange(96 * 96).reshape(96, 96)
+    for l in np.unique(lab[mask]):
+        assert l == idx[lab == l].min()
+
+
 # ------------------------------------------------ planted mistakes (CPU)
 
 MUTANTS = [
@@ -447,6 +494,8 @@ MUTANTS = [
     ("adjoint screen conj dropped", "G[i] = conj(e) * gw + 2.0",
      "G[i] = e * gw + 2.0", "adjoint"),
     ("Strang half screen over the full step", "half.dz = 0.5 * p->dz;", "half.dz = p->dz;", "strang"),
+    ("hot areas joined across the window edge", "if (rr < 0 || rr >= n || cc < 0 || cc >= n) continue;",
+     "rr = (rr + n) % n; cc = (cc + n) % n;", "hot"),
 ]
 
 
@@ -463,6 +512,7 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "fft": lambda: test_fft2_matches_brute_force_dft(8),
         "adjoint": test_adjoint_field_gradient_matches_directional_difference,
         "strang": test_strang_is_second_order_and_lie_first_order,
+        "hot": test_hot_areas_hand_made_patterns,
     }
     with pytest.raises(AssertionError):
         pins[pin]()
