@@ -95,6 +95,8 @@ def _configure(lib):
     lib.orc_march.argtypes = [P, cp, ctypes.c_int, cp, cp]
     lib.orc_march_strang.argtypes = [P, cp, ctypes.c_int, cp, cp]
     lib.orc_hot_areas.argtypes = [cp, ctypes.c_int, ctypes.c_double, ctypes.c_int, cp]
+    lib.orc_turbulent_eps.argtypes = [P, cp, ctypes.c_double, ctypes.c_double, cp]
+    lib.orc_turbulent_screen.argtypes = [P, cp, cp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.orc_hot_areas.restype = ctypes.c_int
     lib.orc_adjoint.argtypes = [P, cp, cp, ctypes.c_int, ctypes.c_int, cp, cp]
     lib.orc_adjoint.restype = ctypes.c_double
@@ -232,6 +234,24 @@ def hot_areas(w, wp: float, conn: int = 4):
     if count < 0:
         raise ValueError("hot_areas: bad argument")
     return int(count), labels
+
+
+def turbulent_eps(xi, cfg: dict, tau: float, kh: float) -> np.ndarray:
+    """Turbulent screen eps_t(y, x) of Eqs. 9-10 from the random draws xi
+    (n x n complex, FFT bin order): step spectrum tau for |k| <= kh."""
+    xi = _c128(xi)
+    out = np.empty(xi.shape, dtype=np.float64)
+    _load().orc_turbulent_eps(ctypes.byref(params(cfg)), xi.ctypes.data, float(tau), float(kh), out.ctypes.data)
+    return out
+
+
+def turbulent_screen(U, xi, cfg: dict, tau: float, kh: float, thickness: float) -> np.ndarray:
+    """U exp(-i thickness eps_t / (2 k0)): the turbulent layer of Eq. 9."""
+    out = _c128(U).copy()
+    xi = _c128(xi)
+    _load().orc_turbulent_screen(ctypes.byref(params(cfg)), out.ctypes.data, xi.ctypes.data, float(tau),
+                                 float(kh), float(thickness))
+    return out
 
 
 def adjoint(U0, D, cfg: dict, nsteps: int, ckpt: int = 20):

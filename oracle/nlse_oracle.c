@@ -413,6 +413,49 @@ int orc_hot_areas(const double *w, int n, double wp, int conn, int32_t *labels) 
     return count;
 }
 
+/* ---------------------------------------------------- turbulent screen -- */
+
+/* Turbulent phase screen of Sec. 3.3 (Eqs. 9-10), built by the spectral method:
+ * its spectral amplitude is a step, tau for spatial frequencies |k| <= k_h (k_h
+ * read as the upper cut-off, so the step is theta(k_h - |k|)) and 0 above, and
+ * the screen is the real part of the unnormalised inverse 2D DFT of that
+ * amplitude times the caller's complex random draws xi (FFT bin order, rows =
+ * k_y, columns = k_x):
+ *   eps_t(y_l, x_j) = Re sum_{q,p} tau [p~^2 + q~^2 <= (k_h L / 2 pi)^2]
+ *                     xi[q][p] exp(+2 pi i (p j + q l) / n),
+ * with p~, q~ the signed bin numbers.  eps_t is written to eps (n*n). */
+void orc_turbulent_eps(const orc_params *p, const cplx *xi, double tau, double kh, double *eps) {
+    int n = p->n;
+    size_t nn = (size_t)n * n;
+    double rc = kh * p->L / (2.0 * M_PI);
+    double r2 = rc * rc;
+    cplx *S = (cplx *)malloc(sizeof(cplx) * nn);
+    for (int q = 0; q < n; ++q) {
+        int qq = (q < n / 2) ? q : q - n;
+        for (int c = 0; c < n; ++c) {
+            int pp = (c < n / 2) ? c : c - n;
+            double m2 = (double)pp * pp + (double)qq * qq;
+            S[(size_t)q * n + c] = (m2 <= r2) ? tau * xi[(size_t)q * n + c] : 0.0;
+        }
+    }
+    orc_fft2d(S, n, 1); /* carries 1/n^2 */
+    for (size_t i = 0; i < nn; ++i) eps[i] = creal(S[i]) * (double)nn;
+    free(S);
+}
+
+/* The screen acts on the field like the other permittivity terms of Eq. 9 over
+ * a layer of the given thickness: U <- U exp(-i thickness eps_t / (2 k0)), the
+ * same form as the nonlinear screen's exp(-i dz/(2 k0) [...]). */
+void orc_turbulent_screen(const orc_params *p, cplx *U, const cplx *xi, double tau, double kh,
+                          double thickness) {
+    size_t nn = (size_t)p->n * p->n;
+    double *eps = (double *)malloc(sizeof(double) * nn);
+    orc_turbulent_eps(p, xi, tau, kh, eps);
+    double c = thickness / (2.0 * wavenumber(p));
+    for (size_t i = 0; i < nn; ++i) U[i] *= cexp(-I * c * eps[i]);
+    free(eps);
+}
+
 /* -------------------------------------------------------------- adjoint -- */
 
 /* Reverse-mode derivative of J(theta, U0) = loss(march(U0, nsteps), D).

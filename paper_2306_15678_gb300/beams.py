@@ -71,3 +71,11 @@ def box_mean(a: np.ndarray, ds: int) -> np.ndarray:
     n = a.shape[0]
     m = n // ds
     return a.reshape(m, ds, m, ds).mean(axis=(1, 3))
+
+
+def turbulence_draws(n: int, seed: int) -> np.ndarray:
+    """The random draws xi of the spectral turbulent screen (Eqs. 9-10): n x n
+    i.i.d. complex unit Gaussians (real and imaginary parts N(0, 1/2); NumPy
+    PCG64, given seed), in FFT bin order."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    return (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * math.sqrt(0.5)

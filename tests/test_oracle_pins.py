@@ -476,6 +476,68 @@ def test_hot_areas_match_library_labelling(conn, density):
         assert l == idx[lab == l].min()
 
 
+# ---------------------------------------- turbulent screen (Eqs. 9-10)
+
+def test_turbulent_eps_single_spectral_line():
+    """One random draw at bin (q0, p0) inside the cut-off: the screen is the
+    single plane wave Re(tau xi e^{2 pi i (p0 x + q0 y)/n}) (the inverse DFT of
+    a delta, evaluated here by direct cos/sin); a draw outside the cut-off
+    (|k| > k_h) gives no screen at all."""
+    n = 32
+    cfg = configs.physics(n, 0.64, 1e-3, configs.KERR)
+    kunit = 2 * math.pi / cfg["L"]
+    for q0, p0 in [(0, 0), (3, 5), (n - 2, 7), (n // 2, 1)]:
+        xi = np.zeros((n, n), complex)
+        a = 0.7 - 1.3j
+        xi[q0, p0] = a
+        eps = oracle.turbulent_eps(xi, cfg, 2.5, 40.0 * kunit)
+        y, x = np.indices((n, n))
+        ph = 2 * math.pi * (p0 * x + q0 * y) / n
+        expect = 2.5 * (a.real * np.cos(ph) - a.imag * np.sin(ph))
+        assert np.max(np.abs(eps - expect)) < 1e-12
+    xi = np.zeros((n, n), complex)
+    xi[0, 6] = xi[n - 4, n - 5] = 1.0  # |k| = 6 and sqrt(41) bins
+    assert np.max(np.abs(oracle.turbulent_eps(xi, cfg, 1.0, 5.5 * kunit))) == 0.0
+    assert np.max(np.abs(oracle.turbulent_eps(xi, cfg, 1.0, 6.5 * kunit))) > 0.5
+
+
+def test_turbulent_eps_cut_off_is_a_disc_in_k():
+    """Step spectrum theta(k_h - |k|): the screen's own 2D spectrum (numpy's
+    FFT) is tau xi on the bins with p~^2 + q~^2 <= (k_h L/2 pi)^2 (up to the
+    Hermitian part, since eps_t is real) and zero outside; its mean is
+    Re(tau xi[0, 0])."""
+    n = 64
+    cfg = configs.physics(n, 0.64, 1e-3, configs.KERR)
+    rng = np.random.default_rng(8)
+    xi = crand((n, n), rng)
+    kunit = 2 * math.pi / cfg["L"]
+    eps = oracle.turbulent_eps(xi, cfg, 3.0, 9.3 * kunit)
+    spec = np.fft.fft2(eps) / n ** 2  # eps = sum of e^{+i k r} terms: the forward DFT / n^2 recovers them
+    m = np.fft.fftfreq(n, 1.0 / n)
+    inside = (m[None, :] ** 2 + m[:, None] ** 2) <= 9.3 ** 2
+    herm = 0.5 * (3.0 * xi * inside + np.conj(np.roll(np.flip(3.0 * xi * inside), 1, axis=(0, 1))))
+    assert np.max(np.abs(spec - herm)) < 1e-12
+    assert abs(eps.mean() - 3.0 * xi[0, 0].real) < 1e-12
+
+
+def test_turbulent_layer_acts_like_the_kerr_term():
+    """Eq. 9 adds eps_t to the same permittivity bracket as the Kerr term of
+    Eq. 1: a turbulent layer whose screen equals eps_k |U|^2 over a thickness dz
+    must reproduce the pinned Kerr screen over dz exactly.  The draws that make
+    eps_t = eps_k |U|^2 are its 2D spectrum (numpy FFT / n^2), cut-off above
+    every bin.  The layer is a pure phase: |U| is unchanged."""
+    n = 32
+    cfg = configs.physics(n, 0.64, 0.37, configs.KERR)
+    v = field_with_intensity(n, 2e12, np.random.default_rng(4))
+    k0 = 2 * math.pi * cfg["n0"] / cfg["lambda0"]
+    eps_k = 2 * k0 * k0 * cfg["n2"] / cfg["n0"]
+    xi = np.fft.fft2(eps_k * np.abs(v) ** 2) / n ** 2
+    kbig = 2 * math.pi / cfg["L"] * n
+    U = oracle.turbulent_screen(v, xi, cfg, 1.0, kbig, cfg["dz"])
+    assert rel_max(np.abs(U), np.abs(v)) < 1e-14
+    assert rel_max(U, oracle.screen(v, cfg)) < 1e-10
+
+
 # ------------------------------------------------ planted mistakes (CPU)
 
 MUTANTS = [
@@ -496,6 +558,15 @@ MUTANTS = [
     ("Strang half screen over the full step", "half.dz = 0.5 * p->dz;", "half.dz = p->dz;", "strang"),
     ("hot areas joined across the window edge", "if (rr < 0 || rr >= n || cc < 0 || cc >= n) continue;",
      "rr = (rr + n) % n; cc = (cc + n) % n;", "hot"),
+    ("turbulent layer sign", "U[i] *= cexp(-I * c * eps[i]);", "U[i] *= cexp(I * c * eps[i]);", "turb_kerr"),
+    ("turbulent layer without the 2 k0", "double c = thickness / (2.0 * wavenumber(p));",
+     "double c = thickness / wavenumber(p);", "turb_kerr"),
+    ("turbulent step read literally as theta(k - k_h)", "S[(size_t)q * n + c] = (m2 <= r2) ?",
+     "S[(size_t)q * n + c] = (m2 > r2) ?", "turb_line"),
+    ("turbulent screen without the n^2 of the unnormalised sum", "eps[i] = creal(S[i]) * (double)nn;",
+     "eps[i] = creal(S[i]);", "turb_line"),
+    ("turbulent screen with x and y swapped", "S[(size_t)q * n + c] = (m2 <= r2) ? tau * xi[(size_t)q * n + c]",
+     "S[(size_t)q * n + c] = (m2 <= r2) ? tau * xi[(size_t)c * n + q]", "turb_line"),
 ]
 
 
@@ -513,6 +584,8 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "adjoint": test_adjoint_field_gradient_matches_directional_difference,
         "strang": test_strang_is_second_order_and_lie_first_order,
         "hot": test_hot_areas_hand_made_patterns,
+        "turb_kerr": test_turbulent_layer_acts_like_the_kerr_term,
+        "turb_line": test_turbulent_eps_single_spectral_line,
     }
     with pytest.raises(AssertionError):
         pins[pin]()
