@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-strang", action="store_true")
+    ap.add_argument("--no-hot", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--large-adjoint-steps", type=int, default=100)
     return ap.parse_args()
@@ -431,6 +432,24 @@ def main():
                     "step_hbm_frac": (2 * bytes_launch) / (ms / args.steps / 1e3) / 1e9 / peak_gbs,
                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_note}
 
+        # ---- hot areas (closed regions with fluence >= 0.01 TW/cm^2) of the marched field
+        hot = None
+        if not args.no_hot:
+            wp = 1.0e10
+            g.hot_areas(wp, 4)
+            ts = []
+            for _ in range(5):
+                h0 = torch.cuda.Event(enable_timing=True)
+                h1 = torch.cuda.Event(enable_timing=True)
+                h0.record(stream)
+                count, _ = g.hot_areas(wp, 4)
+                h1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(h0.elapsed_time(h1))
+            hot = {"w_p_w_per_cm2": wp, "connectivity": 4, "count": count, "ms": min(ts),
+                   "steps_marched": g.steps_taken,
+                   "includes": "fluence readout, run labelling, union-find merge, roots, spread; count to host"}
+
         # ---- symmetric (Strang) steps on the same field: one more screen per row pass
         strang = None
         if not args.no_strang:
@@ -509,7 +528,7 @@ def main():
             "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
-            "strang": strang, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
+            "strang": strang, "hot_areas": hot, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

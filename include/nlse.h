@@ -182,6 +182,43 @@ nlse_status nlse_fluence(nlse_grid* g, void* dst, int dst_on_device, int downsam
  * to dst (host if dst_on_device == 0).  Synchronises when dst is on the host. */
 nlse_status nlse_read_field(nlse_grid* g, void* dst, int dst_on_device);
 
+/* Hot areas of the current cross-section (Sec. 3.3: the closed regions where
+ * the fluence w = U U* reaches the cut-off w_p, whose number the paper tracks
+ * against distance).  A pixel belongs to a region when w >= w_p, both taken in
+ * the grid precision (w_p rounded to float for FP32 grids); regions are the
+ * connected components of those pixels with `connectivity` = 4 (edge
+ * neighbours) or 8 (edges and corners); the window is not periodic.
+ *   count   host int32: the number of regions.
+ *   labels  NULL, or n*n int32 in row-major order (host if labels_on_device ==
+ *           0, else device memory on the grid's stream): -1 outside every
+ *           region, else the smallest row-major index (y*n + x) of the pixel's
+ *           region, so that labels are unique and independent of the order in
+ *           which the device joins pixels.
+ * NLSE_EINVAL for a bad argument (w_p not finite, connectivity not 4 or 8);
+ * NLSE_ESTATE before a field is loaded.  Synchronises. */
+nlse_status nlse_hot_areas(nlse_grid* g, double w_p, int32_t connectivity, int32_t* count,
+                           int32_t* labels, int labels_on_device);
+
+/* Pass the current field through a turbulent layer (Sec. 3.3, Eqs. 9-10): the
+ * random permittivity screen eps_t enters Eq. 9 beside the other terms, so a
+ * layer of the given thickness (cm) multiplies the field by
+ * exp(-i thickness eps_t / (2 k0)), k0 = 2 pi n0 / lambda0.  eps_t is built by
+ * the spectral method with the step spectrum of Eq. 10, read as amplitude tau
+ * for |k| <= k_h (k_h the upper cut-off, rad/cm) and 0 above:
+ *   eps_t(y_l, x_j) = Re sum_{q,p} tau [p~^2 + q~^2 <= (k_h L / 2 pi)^2]
+ *                     xi[q][p] exp(+2 pi i (p j + q l) / n),
+ * p~, q~ the signed bin numbers (p~ = p for p < n/2, else p - n).
+ *   xi  n*n complex of the grid precision (interleaved re, im), row q = k_y
+ *       bin, column p = k_x bin: the caller's random draws (e.g. complex unit
+ *       Gaussians), host if xi_on_device == 0, else device memory that is
+ *       only read.
+ * Between z steps only; the step count and the recorded history are kept.
+ * NLSE_EINVAL for a bad argument (tau, thickness not finite, k_h negative or
+ * not finite); NLSE_ESTATE before a field is loaded.  Asynchronous when xi is
+ * on the device. */
+nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device, double tau,
+                                  double k_h, double thickness);
+
 /* Copy up to `capacity` recorded (power, peak) pairs, oldest first, into
  * power[] and peak[] (host arrays; either may be NULL) and their count into
  * *count.  Entry i was recorded after (i+1)*diag_every steps.  The history

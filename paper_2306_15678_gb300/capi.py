@@ -76,6 +76,10 @@ _SIGS = {
     "nlse_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "nlse_fluence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "nlse_read_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_hot_areas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "nlse_turbulent_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double]),
     "nlse_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]),
     "nlse_device_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -198,6 +202,18 @@ def nlse_fluence(h, dst: int, on_device: bool, downsample: int) -> None:
 
 def nlse_read_field(h, dst: int, on_device: bool) -> None:
     check(lib().nlse_read_field(h, ctypes.c_void_p(dst), int(bool(on_device))), "nlse_read_field")
+
+
+def nlse_hot_areas(h, w_p: float, connectivity: int, labels_ptr: int, on_device: bool) -> int:
+    c = ctypes.c_int32(0)
+    check(lib().nlse_hot_areas(h, float(w_p), int(connectivity), ctypes.byref(c),
+                               ctypes.c_void_p(labels_ptr or None), int(bool(on_device))), "nlse_hot_areas")
+    return int(c.value)
+
+
+def nlse_turbulent_screen(h, xi_ptr: int, on_device: bool, tau: float, k_h: float, thickness: float) -> None:
+    check(lib().nlse_turbulent_screen(h, ctypes.c_void_p(xi_ptr), int(bool(on_device)), float(tau), float(k_h),
+                                      float(thickness)), "nlse_turbulent_screen")
 
 
 def nlse_history(h, power_ptr: int, peak_ptr: int, capacity: int) -> int:

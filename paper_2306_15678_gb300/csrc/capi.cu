@@ -15,6 +15,7 @@
 
 #include "../../include/nlse.h"
 #include "dispatch.cuh"
+#include "hot_areas.cuh"
 #include "host_detail.h"
 
 using namespace nlse;
@@ -713,6 +714,87 @@ nlse_status nlse_read_field(nlse_grid* g, void* dst, int dst_on_device) {
             return NLSE_ECUDA;
         return cuerr(cudaStreamSynchronize(g->stream));
     }
+    return NLSE_OK;
+}
+
+nlse_status nlse_hot_areas(nlse_grid* g, double w_p, int32_t connectivity, int32_t* count, int32_t* labels,
+                           int labels_on_device) {
+    if (!g || !count || !std::isfinite(w_p) || (connectivity != 4 && connectivity != 8)) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    const int n = g->p.n;
+    const int nn = n * n;
+    const bool f64 = g->p.precision == NLSE_FP64;
+    unsigned char* flu = g->ws + g->lay.aux;  // n^2 reals; the labels use the second half of aux
+    int* lab = labels && labels_on_device ? labels : reinterpret_cast<int*>(flu + (size_t)nn * (f64 ? 8 : 4));
+    nlse_status st = readout_any(g, nullptr, flu);
+    if (st != NLSE_OK) return st;
+    // the readout's finalisation has consumed the partials: they hold {count, status} now
+    int* word = reinterpret_cast<int*>(dat(g, g->lay.partials));
+    if (cudaMemsetAsync(word, 0, 2 * sizeof(int), g->stream) != cudaSuccess) return NLSE_ECUDA;
+    const int rt = n < 256 ? n : 256;
+    if (f64) k_hot_runs<double><<<n, rt, 0, g->stream>>>((const double*)flu, n, w_p, lab);
+    else k_hot_runs<float><<<n, rt, 0, g->stream>>>((const float*)flu, n, (float)w_p, lab);
+    const int blocks = std::min((nn + 255) / 256, 152 * 8);
+    k_hot_merge<<<blocks, 256, 0, g->stream>>>(lab, n, connectivity, word + 1);
+    k_hot_roots<<<blocks, 256, 0, g->stream>>>(lab, n, word);
+    k_hot_spread<<<blocks, 256, 0, g->stream>>>(lab, nn);
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    int host_word[2] = {0, 0};
+    if (cudaMemcpyAsync(host_word, word, sizeof(host_word), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (labels && !labels_on_device &&
+        cudaMemcpyAsync(labels, lab, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return NLSE_ECUDA;
+    if (host_word[1] & kHotStatusGaveUp) return NLSE_ETIMEOUT;
+    *count = host_word[0];
+    return NLSE_OK;
+}
+
+nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device, double tau, double k_h,
+                                  double thickness) {
+    if (!g || !xi || !std::isfinite(tau) || !std::isfinite(k_h) || !(k_h >= 0.0) || !std::isfinite(thickness))
+        return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    const int n = g->p.n;
+    const bool f64 = g->p.precision == NLSE_FP64;
+    const size_t nn = (size_t)n * n;
+    const size_t bytes = nn * (f64 ? 16 : 8);
+    unsigned char* field = g->ws + g->lay.aux;
+    unsigned char* spec = g->ws + g->lay.state;
+    // the field leaves the state for the scratch buffer (row-major, global
+    // phase removed); the state buffer then holds the screen while it is built
+    nlse_status st = readout_any(g, field, nullptr);
+    if (st != NLSE_OK) return st;
+    const void* src = xi;
+    if (!xi_on_device) {
+        if (cudaMemcpyAsync(spec, xi, bytes, cudaMemcpyHostToDevice, g->stream) != cudaSuccess) return NLSE_ECUDA;
+        src = spec;
+    }
+    const double rc = k_h * g->p.L / kTwoPi;
+    const double r2 = rc * rc;
+    const double c = thickness / (2.0 * (kTwoPi * g->p.n0 / g->p.lambda0));
+    const int blocks = (int)std::min<size_t>((nn + 255) / 256, 152 * 8);
+    cudaError_t e;
+    if (f64) {
+        k_turb_spectrum<double><<<blocks, 256, 0, g->stream>>>((const double2*)src, (double2*)spec, n, tau, r2);
+        e = g->k64->idft2((double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw), g->stream);
+        if (e == cudaSuccess) {
+            k_turb_apply<double><<<blocks, 256, 0, g->stream>>>((double2*)field, (const double2*)spec, c, nn);
+            e = g->k64->row_forward((const double2*)field, (double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw),
+                                    g->stream);
+        }
+    } else {
+        k_turb_spectrum<float><<<blocks, 256, 0, g->stream>>>((const float2*)src, (float2*)spec, n, tau, r2);
+        e = g->k32->idft2((float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw), g->stream);
+        if (e == cudaSuccess) {
+            k_turb_apply<float><<<blocks, 256, 0, g->stream>>>((float2*)field, (const float2*)spec, c, nn);
+            e = g->k32->row_forward((const float2*)field, (float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw),
+                                    g->stream);
+        }
+    }
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    g->theta = 0.0;  // the readout removed the accumulated global phase
     return NLSE_OK;
 }
 

@@ -1,0 +1,65 @@
+// turbulence.cuh -- kernels of the turbulent layer (arXiv 2306.15678, Sec. 3.3,
+// Eqs. 9-10): the step spectrum of the random screen, the unnormalised inverse
+// 2D DFT that turns it into the permittivity screen eps_t, and the layer's
+// phase factor exp(-i thickness eps_t / (2 k0)) on the row-major field.
+#pragma once
+#include "kernels.cuh"
+
+namespace nlse {
+
+// Spectral amplitude of the turbulent screen: out = tau xi on the bins with
+// p~^2 + q~^2 <= r2 (r2 = (k_h L / 2 pi)^2, signed bin numbers), 0 elsewhere;
+// row-major, rows = k_y.  out may alias xi.
+template <typename T>
+__global__ void k_turb_spectrum(const typename vec2<T>::type* xi, typename vec2<T>::type* out, int n, double tau,
+                                double r2) {
+    const size_t nn = (size_t)n * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(i / n), p = (int)(i % n);
+        const int qq = q < n / 2 ? q : q - n, pp = p < n / 2 ? p : p - n;
+        const double m2 = (double)pp * pp + (double)qq * qq;
+        const typename vec2<T>::type v = xi[i];
+        out[i] = m2 <= r2 ? mk<typename vec2<T>::type>((T)(tau * (double)v.x), (T)(tau * (double)v.y))
+                          : mk<typename vec2<T>::type>((T)0, (T)0);
+    }
+}
+
+// Unnormalised inverse DFT of every line of a row-major n x n array, in place:
+// rows (along x) when COLS is false, columns (along y) when true.  Every line
+// is loaded before the first exchange barrier and stored after the last, so
+// the transform may overwrite its input.
+template <typename T, int N, bool COLS>
+__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
+                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
+k_idft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __restrict__ tw) {
+    using V = typename vec2<T>::type;
+    constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
+    constexpr int LS = line_stride<T, N, RPB>();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* smem = reinterpret_cast<V*>(smraw);
+    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
+    const size_t line = (size_t)blockIdx.x * RPB + g;
+    const size_t base = COLS ? line : line * N, stride = COLS ? N : 1;
+    V v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = data[base + (size_t)(j + m * TL) * stride];
+    fft_stockham<V, N, E, true>(v, smem + g * LS, tw, j);
+#pragma unroll
+    for (int m = 0; m < E; ++m) data[base + (size_t)(j + m * TL) * stride] = v[m];
+}
+
+// The turbulent layer on the row-major field: U <- U exp(-i c Re(eps)), the
+// phase taken in FP64 (c = thickness / (2 k0)).
+template <typename T>
+__global__ void k_turb_apply(typename vec2<T>::type* field, const typename vec2<T>::type* __restrict__ eps,
+                             double c, size_t nn) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincos(-c * (double)eps[i].x, &sn, &cs);
+        const typename vec2<T>::type u = field[i];
+        field[i] = mk<typename vec2<T>::type>((T)((double)u.x * cs - (double)u.y * sn),
+                                              (T)((double)u.x * sn + (double)u.y * cs));
+    }
+}
+
+}  // namespace nlse

@@ -110,6 +110,32 @@ class Grid:
         capi.nlse_fluence(self.h, out.ctypes.data, False, downsample)
         return out
 
+    def hot_areas(self, w_p: float, connectivity: int = 4, labels: bool = False, device: bool = False):
+        """Number of hot areas (regions with fluence >= w_p, Sec. 3.3) and, with
+        labels=True, the n x n int32 labels (-1 outside, else the smallest
+        row-major index of the region): (count, labels or None)."""
+        if not labels:
+            return capi.nlse_hot_areas(self.h, w_p, connectivity, 0, False), None
+        if device:
+            out = torch.empty((self.n, self.n), dtype=torch.int32, device=self.device)
+            return capi.nlse_hot_areas(self.h, w_p, connectivity, out.data_ptr(), True), out
+        out = np.empty((self.n, self.n), dtype=np.int32)
+        return capi.nlse_hot_areas(self.h, w_p, connectivity, out.ctypes.data, False), out
+
+    def turbulent_screen(self, xi, tau: float, k_h: float, thickness: float) -> "Grid":
+        """Turbulent layer of Eqs. 9-10: U <- U exp(-i thickness eps_t / (2 k0)),
+        eps_t the spectral screen of the draws xi (n x n complex, FFT bin order)
+        with step amplitude tau up to the cut-off k_h (rad/cm)."""
+        if isinstance(xi, torch.Tensor) and xi.is_cuda:
+            t = xi.to(self.tcdtype).contiguous()
+            capi.nlse_turbulent_screen(self.h, t.data_ptr(), True, tau, k_h, thickness)
+            self._keep = t
+        else:
+            a = np.ascontiguousarray(xi.cpu().numpy() if isinstance(xi, torch.Tensor) else xi, dtype=self.cdtype)
+            assert a.shape == (self.n, self.n)
+            capi.nlse_turbulent_screen(self.h, a.ctypes.data, False, tau, k_h, thickness)
+        return self
+
     def history(self):
         cap = 4096
         pw = np.empty(cap)
