@@ -63,6 +63,39 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+LENS_SEG = 8
+
+
+class OrcLens(ctypes.Structure):
+    _fields_ = [
+        ("l_dif", ctypes.c_double),
+        ("w_l", ctypes.c_double),
+        ("conn", ctypes.c_int32),
+        ("n_re", ctypes.c_int32),
+        ("n_im", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ] + [(f, ctypes.c_double * LENS_SEG) for f in ("r_re", "a", "omega", "psi", "r_im", "b", "nu", "eta")]
+
+
+def lens_record(lens: dict) -> OrcLens:
+    """Pack an effective-lens dict -- l_dif (cm^2), w_l (W/cm^2), conn (4/8),
+    re = [(r_j, a_j, omega_j, psi_j), ...], im = [(r_l, b_l, nu_l, eta_l), ...]
+    (joints in cm, increasing) -- into the oracle's record."""
+    q = OrcLens()
+    q.l_dif = float(lens["l_dif"])
+    q.w_l = float(lens["w_l"])
+    q.conn = int(lens.get("conn", 4))
+    for part, names, cnt in (("re", ("r_re", "a", "omega", "psi"), "n_re"),
+                             ("im", ("r_im", "b", "nu", "eta"), "n_im")):
+        segs = lens.get(part, ())
+        assert len(segs) <= LENS_SEG
+        setattr(q, cnt, len(segs))
+        for j, seg in enumerate(segs):
+            for f, v in zip(names, seg):
+                getattr(q, f)[j] = float(v)
+    return q
+
+
 def build(force: bool = False) -> str:
     """Compile nlse_oracle.c into _build/liboracle.so with gcc (FP64, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -96,6 +129,12 @@ def _configure(lib):
     lib.orc_march_strang.argtypes = [P, cp, ctypes.c_int, cp, cp]
     lib.orc_hot_areas.argtypes = [cp, ctypes.c_int, ctypes.c_double, ctypes.c_int, cp]
     lib.orc_turbulent_eps.argtypes = [P, cp, ctypes.c_double, ctypes.c_double, cp]
+    LP = ctypes.POINTER(OrcLens)
+    lib.orc_lens_lowpass.argtypes = [ctypes.c_int, ctypes.c_double, cp, ctypes.c_double, cp]
+    lib.orc_lens_centres.argtypes = [cp, ctypes.c_int, ctypes.c_double, ctypes.c_int, cp]
+    lib.orc_lens_value.argtypes = [LP, ctypes.c_double, cp, cp]
+    lib.orc_lens_apply.argtypes = [ctypes.c_int, ctypes.c_double, cp, cp, ctypes.c_int, LP]
+    lib.orc_effective_lens.argtypes = [P, cp, LP, cp]
     lib.orc_turbulent_screen.argtypes = [P, cp, cp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.orc_hot_areas.restype = ctypes.c_int
     lib.orc_adjoint.argtypes = [P, cp, cp, ctypes.c_int, ctypes.c_int, cp, cp]
@@ -252,6 +291,53 @@ def turbulent_screen(U, xi, cfg: dict, tau: float, kh: float, thickness: float) 
     _load().orc_turbulent_screen(ctypes.byref(params(cfg)), out.ctypes.data, xi.ctypes.data, float(tau),
                                  float(kh), float(thickness))
     return out
+
+
+def lens_lowpass(w, L: float, l_dif: float) -> np.ndarray:
+    """Eq. 4: F^-1 exp(-l_dif k^2) F w (real part), k in rad/cm on the window L."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty_like(w)
+    _load().orc_lens_lowpass(w.shape[0], float(L), w.ctypes.data, float(l_dif), out.ctypes.data)
+    return out
+
+
+def lens_centres(w_dif, w_l: float, conn: int = 4) -> np.ndarray:
+    """Row-major indices (increasing) of the lens centres: the maximum of each
+    region with w_dif >= w_l (first in row-major order on a tie)."""
+    wd = np.ascontiguousarray(w_dif, dtype=np.float64)
+    out = np.empty(wd.size, dtype=np.int32)
+    k = _load().orc_lens_centres(wd.ctypes.data, wd.shape[0], float(w_l), int(conn), out.ctypes.data)
+    if k < 0:
+        raise ValueError("lens_centres: bad argument")
+    return out[:k].copy()
+
+
+def lens_value(lens: dict, r: float):
+    """Eq. 6 at distance r: (Re f_lens, Im f_lens)."""
+    re, im = ctypes.c_double(0), ctypes.c_double(0)
+    q = lens_record(lens)
+    _load().orc_lens_value(ctypes.byref(q), float(r), ctypes.byref(re), ctypes.byref(im))
+    return re.value, im.value
+
+
+def lens_apply(U, L: float, centres, lens: dict) -> np.ndarray:
+    """U exp(i D_f), D_f = sum over centres of f_lens(|r - r_c|) (Eqs. 2, 5)."""
+    out = _c128(U).copy()
+    c = np.ascontiguousarray(centres, dtype=np.int32)
+    q = lens_record(lens)
+    _load().orc_lens_apply(out.shape[0], float(L), out.ctypes.data, c.ctypes.data, len(c), ctypes.byref(q))
+    return out
+
+
+def effective_lens(U, cfg: dict, lens: dict):
+    """The whole effective-lens screen: (U exp(i D_f[U]), centres)."""
+    out = _c128(U).copy()
+    cent = np.empty(out.size, dtype=np.int32)
+    q = lens_record(lens)
+    k = _load().orc_effective_lens(ctypes.byref(params(cfg)), out.ctypes.data, ctypes.byref(q), cent.ctypes.data)
+    if k < 0:
+        raise ValueError("effective_lens: bad argument")
+    return out, cent[:k].copy()
 
 
 def adjoint(U0, D, cfg: dict, nsteps: int, ckpt: int = 20):

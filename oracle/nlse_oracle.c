@@ -43,7 +43,10 @@
  * plasma and absorption identities for the screen; power conservation, time
  * reversal, the discrete energy balance and mirror/transpose symmetry for the
  * march; central finite differences for the adjoint; math.fsum / brute force
- * for the readouts and the loss.
+ * for the readouts and the loss; hand-counted patterns and scipy.ndimage.label
+ * for the hot areas; single spectral lines and the Kerr screen for the
+ * turbulent layer; the heat-kernel closed form, hand-made lenses and the
+ * single-centre screen for the effective lens.
  */
 #define _POSIX_C_SOURCE 200809L
 #define _DEFAULT_SOURCE 1
@@ -454,6 +457,119 @@ void orc_turbulent_screen(const orc_params *p, cplx *U, const cplx *xi, double t
     double c = thickness / (2.0 * wavenumber(p));
     for (size_t i = 0; i < nn; ++i) U[i] *= cexp(-I * c * eps[i]);
     free(eps);
+}
+
+/* ------------------------------------------------------ effective lens -- */
+
+/* Effective-lens screen of Sec. 2 (Eqs. 4-6).  Its parameters: the low-pass
+ * length l_dif (cm^2) of Eq. 4, the trimming level w_l (W/cm^2), the neighbours
+ * that join lens pixels (4 or 8), and the radial ansatz of Eq. 6: n_re
+ * segments of the real part, segment j covering r_re[j-1] <= r < r_re[j]
+ * (r_re[-1] = 0) with value a[j] cos(omega[j] r + psi[j]), and n_im segments of
+ * the imaginary part with b, nu, eta; zero beyond the last joint. */
+#define ORC_LENS_SEG 8
+typedef struct {
+    double l_dif, w_l;
+    int32_t conn, n_re, n_im, reserved;
+    double r_re[ORC_LENS_SEG], a[ORC_LENS_SEG], omega[ORC_LENS_SEG], psi[ORC_LENS_SEG];
+    double r_im[ORC_LENS_SEG], b[ORC_LENS_SEG], nu[ORC_LENS_SEG], eta[ORC_LENS_SEG];
+} orc_lens;
+
+/* Eq. 4: w_dif = F^-1 exp(-l_dif k^2) F w, read with k^2 = kx^2 + ky^2 (the
+ * printed exp(-l_dif) lacks its argument; a Gaussian low-pass is the operator
+ * that widens every maximum and keeps w_dif decreasing away from it). */
+void orc_lens_lowpass(int n, double L, const double *w, double l_dif, double *out) {
+    size_t nn = (size_t)n * n;
+    cplx *W = (cplx *)malloc(sizeof(cplx) * nn);
+    for (size_t i = 0; i < nn; ++i) W[i] = w[i];
+    orc_fft2d(W, n, 0);
+    for (int r = 0; r < n; ++r) {
+        double ky = kfreq(r, n, L);
+        for (int c = 0; c < n; ++c) {
+            double kx = kfreq(c, n, L);
+            W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx + ky * ky));
+        }
+    }
+    orc_fft2d(W, n, 1);
+    for (size_t i = 0; i < nn; ++i) out[i] = creal(W[i]);
+    free(W);
+}
+
+static int cmp_i32(const void *x, const void *y) {
+    int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* Lens centres: the regions of w_dif >= w_l (trimming, Fig. 1) are the
+ * disconnected lenses; the centre of each is its pixel of largest w_dif (the
+ * first in row-major order on a tie).  Writes the centres' row-major indices
+ * in increasing order to centres (room for n*n) and returns their number, or
+ * -1 for a bad argument. */
+int orc_lens_centres(const double *wd, int n, double w_l, int conn, int32_t *centres) {
+    size_t nn = (size_t)n * n;
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int count = orc_hot_areas(wd, n, w_l, conn, lab);
+    if (count < 0) { free(lab); return -1; }
+    int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nn);  /* per region root: pixel of the maximum */
+    for (size_t i = 0; i < nn; ++i) best[i] = -1;
+    for (size_t i = 0; i < nn; ++i) {
+        int32_t root = lab[i];
+        if (root < 0) continue;
+        if (best[root] < 0 || wd[i] > wd[best[root]]) best[root] = (int32_t)i;
+    }
+    int k = 0;
+    for (size_t i = 0; i < nn; ++i)
+        if (lab[i] == (int32_t)i) centres[k++] = best[i];
+    qsort(centres, (size_t)k, sizeof(int32_t), cmp_i32);
+    free(best);
+    free(lab);
+    return k;
+}
+
+/* Eq. 6: the radial ansatz at distance r (cm) from a lens centre */
+void orc_lens_value(const orc_lens *ls, double r, double *re, double *im) {
+    *re = 0.0;
+    *im = 0.0;
+    for (int j = 0; j < ls->n_re; ++j)
+        if (r < ls->r_re[j]) { *re = ls->a[j] * cos(ls->omega[j] * r + ls->psi[j]); break; }
+    for (int j = 0; j < ls->n_im; ++j)
+        if (r < ls->r_im[j]) { *im = ls->b[j] * cos(ls->nu[j] * r + ls->eta[j]); break; }
+}
+
+/* Eq. 5 and the screen of Eq. 2: D_f(r) = sum over the centres (in the given
+ * order) of f_lens(|r - r_c|), the distance taken across the window (not
+ * periodic); the screen enters Eq. 2 as exp(-i(h l_f/(2 k0) - f_lens)), so the
+ * field is multiplied by exp(+i D_f): U <- U exp(i Re D_f - Im D_f). */
+void orc_lens_apply(int n, double L, cplx *U, const int32_t *centres, int count, const orc_lens *ls) {
+    double dx = L / n;
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double dre = 0.0, dim = 0.0;
+            for (int c = 0; c < count; ++c) {
+                int xc = centres[c] % n, yc = centres[c] / n;
+                double r = dx * sqrt((double)(x - xc) * (x - xc) + (double)(y - yc) * (y - yc));
+                double fr, fi;
+                orc_lens_value(ls, r, &fr, &fi);
+                dre += fr;
+                dim += fi;
+            }
+            U[(size_t)y * n + x] *= cexp(I * (dre + I * dim));
+        }
+}
+
+/* The whole effective-lens screen on U: fluence, Eq. 4 low-pass, trimming and
+ * centres, Eqs. 5-6.  Returns the number of lenses and writes their centres
+ * (room for n*n), or -1 for a bad argument. */
+int orc_effective_lens(const orc_params *p, cplx *U, const orc_lens *ls, int32_t *centres) {
+    int n = p->n;
+    size_t nn = (size_t)n * n;
+    double *w = (double *)malloc(sizeof(double) * nn);
+    for (size_t i = 0; i < nn; ++i) w[i] = creal(U[i] * conj(U[i]));
+    orc_lens_lowpass(n, p->L, w, ls->l_dif, w);
+    int count = orc_lens_centres(w, n, ls->w_l, ls->conn, centres);
+    if (count >= 0) orc_lens_apply(n, p->L, U, centres, count, ls);
+    free(w);
+    return count;
 }
 
 /* -------------------------------------------------------------- adjoint -- */

@@ -538,6 +538,111 @@ def test_turbulent_layer_acts_like_the_kerr_term():
     assert rel_max(U, oracle.screen(v, cfg)) < 1e-10
 
 
+# ------------------------------------------- effective lens (Eqs. 4-6)
+
+def test_lens_lowpass_gaussian_closed_form():
+    """Eq. 4 on a well-resolved Gaussian: the low-pass exp(-l k^2) is the heat
+    kernel, so exp(-r^2/s^2) becomes s^2/(s^2 + 4 l) exp(-r^2/(s^2 + 4 l))
+    (continuous Fourier transform; aliasing below 1e-60 here).  l = 0 is the
+    identity and a constant is kept."""
+    n, L = 128, 1.28
+    dx = L / n
+    s = 8 * dx
+    y, x = np.indices((n, n))
+    r2 = ((x - 64) ** 2 + (y - 64) ** 2) * dx * dx
+    w = np.exp(-r2 / s ** 2)
+    for l in (1e-5, 4e-5, 1.5e-4):
+        out = oracle.lens_lowpass(w, L, l)
+        s2 = s * s + 4 * l
+        assert np.max(np.abs(out - s * s / s2 * np.exp(-r2 / s2))) < 1e-12
+    assert np.max(np.abs(oracle.lens_lowpass(w, L, 0.0) - w)) < 1e-14
+    assert np.max(np.abs(oracle.lens_lowpass(np.full((n, n), 3.0), L, 1e-3) - 3.0)) < 1e-13
+    # anisotropic input: the low-pass acts along both axes (a line along x keeps its x profile)
+    line = np.zeros((n, n))
+    line[64, :] = 1.0
+    out = oracle.lens_lowpass(line, L, 1e-4)
+    assert np.max(np.abs(out - out[:, :1])) < 1e-13
+    assert out[64, 0] < 0.5
+
+
+def test_lens_centres_hand_made():
+    """Trimming at w_l leaves disconnected lenses; each centre is the lens's
+    largest w_dif, the first in row-major order on a plateau."""
+    w = np.zeros((8, 8))
+    w[1, 1], w[1, 2], w[2, 1] = 5.0, 7.0, 6.0        # lens A, maximum at (1, 2)
+    w[5, 5] = w[5, 6] = w[6, 5] = 4.0                # lens B, a plateau: first is (5, 5)
+    w[3, 7] = 0.5                                    # below the level
+    c = oracle.lens_centres(w, 1.0, 4)
+    assert c.tolist() == [1 * 8 + 2, 5 * 8 + 5]
+    w[3, 3] = w[4, 4] = 2.0                          # a diagonal chain to B: joined with 8 neighbours only
+    assert oracle.lens_centres(w, 1.0, 4).tolist() == [1 * 8 + 2, 3 * 8 + 3, 4 * 8 + 4, 5 * 8 + 5]
+    assert oracle.lens_centres(w, 1.0, 8).tolist() == [1 * 8 + 2, 5 * 8 + 5]
+    assert oracle.lens_centres(np.zeros((8, 8)), 1.0, 4).size == 0
+
+
+LENS1 = dict(l_dif=0.0, w_l=1.0, conn=4,
+             re=[(0.02, 0.8, 60.0, 0.3), (0.05, -0.4, 25.0, 1.1)],
+             im=[(0.03, 0.2, 40.0, -0.5)])
+
+
+def test_lens_value_is_piecewise_eq6():
+    """Eq. 6: segment j holds on r_{j-1} <= r < r_j (r_0 = 0); zero past the
+    last joint; real and imaginary parts have their own joints."""
+    for r, re, im in [(0.0, 0.8 * math.cos(0.3), 0.2 * math.cos(-0.5)),
+                      (0.019, 0.8 * math.cos(60 * 0.019 + 0.3), 0.2 * math.cos(40 * 0.019 - 0.5)),
+                      (0.02, -0.4 * math.cos(25 * 0.02 + 1.1), 0.2 * math.cos(40 * 0.02 - 0.5)),
+                      (0.03, -0.4 * math.cos(25 * 0.03 + 1.1), 0.0),
+                      (0.05, 0.0, 0.0), (1.0, 0.0, 0.0)]:
+        got = oracle.lens_value(LENS1, r)
+        assert abs(got[0] - re) < 1e-15 and abs(got[1] - im) < 1e-15, r
+
+
+def test_lens_apply_closed_form_and_superposition():
+    """Eqs. 2 and 5 for a plane field: one centre multiplies U by
+    exp(i Re f(r)) exp(-Im f(r)) with r the distance across the window (a
+    centre next to the edge does not wrap); two centres multiply the two
+    single-centre screens (the sum over centres of Eq. 5)."""
+    n, L = 64, 0.64
+    dx = L / n
+    U = np.full((n, n), 2.0 + 1.0j)
+    y, x = np.indices((n, n))
+
+    def single(c):
+        r = dx * np.sqrt((x - c % n) ** 2.0 + (y - c // n) ** 2.0)
+        re = np.where(r < 0.02, 0.8 * np.cos(60 * r + 0.3), np.where(r < 0.05, -0.4 * np.cos(25 * r + 1.1), 0.0))
+        im = np.where(r < 0.03, 0.2 * np.cos(40 * r - 0.5), 0.0)
+        return np.exp(1j * re - im)
+
+    c1, c2 = 2 * n + 1, 40 * n + 30
+    out = oracle.lens_apply(U, L, [c1], LENS1)
+    assert np.max(np.abs(out - U * single(c1))) < 1e-13
+    out = oracle.lens_apply(U, L, [c1, c2], LENS1)
+    assert np.max(np.abs(out - U * single(c1) * single(c2))) < 1e-13
+
+
+def test_effective_lens_finds_planted_spots():
+    """The whole screen on a field with two hot spots on a weak background:
+    after the low-pass the lenses are centred on the spots' peaks (symmetric
+    spots keep their maxima), and the field changes only within the ansatz's
+    reach of them."""
+    cfg = configs.physics(128, 1.28, 1.0, configs.KERR)
+    n, dx = 128, 0.01
+    y, x = np.indices((n, n))
+    spots = [(40, 30), (90, 100)]
+    w = 1e11 * np.exp(-((x - 64.0) ** 2 + (y - 64.0) ** 2) * dx * dx / 0.3 ** 2)
+    for (sy, sx) in spots:
+        w = w + 5e12 * np.exp(-((x - sx) ** 2 + (y - sy) ** 2) * dx * dx / 0.02 ** 2)
+    U = np.sqrt(w) * np.exp(0.3j)
+    lens = dict(LENS1, l_dif=2e-5, w_l=1e12)
+    out, cent = oracle.effective_lens(U, cfg, lens)
+    assert cent.tolist() == sorted(sy * n + sx for sy, sx in spots)
+    far = np.ones((n, n), bool)
+    for (sy, sx) in spots:
+        far &= (x - sx) ** 2 + (y - sy) ** 2 >= 25 ** 2
+    assert np.array_equal(out[far], U[far])
+    assert not np.allclose(out[~far], U[~far])
+
+
 # ------------------------------------------------ planted mistakes (CPU)
 
 MUTANTS = [
@@ -565,6 +670,18 @@ MUTANTS = [
      "S[(size_t)q * n + c] = (m2 > r2) ?", "turb_line"),
     ("turbulent screen without the n^2 of the unnormalised sum", "eps[i] = creal(S[i]) * (double)nn;",
      "eps[i] = creal(S[i]);", "turb_line"),
+    ("low-pass sign", "W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx + ky * ky));",
+     "W[(size_t)r * n + c] *= exp(l_dif * (kx * kx + ky * ky));", "lens_gauss"),
+    ("low-pass along x only", "W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx + ky * ky));",
+     "W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx));", "lens_gauss"),
+    ("lens centre = last maximum on a plateau", "if (best[root] < 0 || wd[i] > wd[best[root]])",
+     "if (best[root] < 0 || wd[i] >= wd[best[root]])", "lens_centres"),
+    ("lens segment closed at its joint", "if (r < ls->r_re[j]) { *re", "if (r <= ls->r_re[j]) { *re", "lens_value"),
+    ("lens screen sign", "U[(size_t)y * n + x] *= cexp(I * (dre + I * dim));",
+     "U[(size_t)y * n + x] *= cexp(-I * (dre + I * dim));", "lens_apply"),
+    ("lens distance wrapped across the window", "int xc = centres[c] % n, yc = centres[c] / n;",
+     "int xc = centres[c] % n, yc = centres[c] / n; if (x - xc > n / 2) xc += n; if (xc - x > n / 2) xc -= n;",
+     "lens_apply"),
     ("turbulent screen with x and y swapped", "S[(size_t)q * n + c] = (m2 <= r2) ? tau * xi[(size_t)q * n + c]",
      "S[(size_t)q * n + c] = (m2 <= r2) ? tau * xi[(size_t)c * n + q]", "turb_line"),
 ]
@@ -586,6 +703,10 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "hot": test_hot_areas_hand_made_patterns,
         "turb_kerr": test_turbulent_layer_acts_like_the_kerr_term,
         "turb_line": test_turbulent_eps_single_spectral_line,
+        "lens_gauss": test_lens_lowpass_gaussian_closed_form,
+        "lens_centres": test_lens_centres_hand_made,
+        "lens_value": test_lens_value_is_piecewise_eq6,
+        "lens_apply": test_lens_apply_closed_form_and_superposition,
     }
     with pytest.raises(AssertionError):
         pins[pin]()
