@@ -219,6 +219,55 @@ nlse_status nlse_hot_areas(nlse_grid* g, double w_p, int32_t connectivity, int32
 nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device, double tau,
                                   double k_h, double thickness);
 
+/* Effective lens (Sec. 2, Eqs. 4-6; Fig. 1): the screen that replaces the
+ * filamentation region on a sparse grid once the intensity reaches the
+ * pre-filamentation level.  Built from the current field:
+ *   1. w = U U*; Eq. 4 low-pass w_dif = F^-1 exp(-l_dif k^2) F w (k^2 = kx^2 + ky^2);
+ *   2. trimming: the lenses are the connected regions of w_dif >= w_l
+ *      (4 or 8 neighbours, window not periodic, compared in grid precision);
+ *   3. each lens is centred on its pixel of largest w_dif (first in row-major
+ *      order on a tie);
+ *   4. Eqs. 5-6: D_f(r) = sum over the centres, in increasing row-major index,
+ *      of f_lens(|r - r_c|), with the piecewise radial ansatz of Eq. 6: real
+ *      part a_j cos(omega_j r + psi_j) on r_re[j-1] <= r < r_re[j] (r_re[-1] = 0,
+ *      j < n_re), imaginary part b_l cos(nu_l r + eta_l) on its own joints r_im,
+ *      zero beyond the last joint; distances in cm across the window;
+ *   5. the screen enters Eq. 2 as exp(-i(h l_f/(2 k0) - f_lens)): the field is
+ *      multiplied by exp(+i D_f) = exp(i Re D_f) exp(-Im D_f).
+ * The diffraction over the lens length l_f is the caller's (a diffraction-only
+ * grid marched over l_f, or the ordinary march).  FP64 for the ansatz and the
+ * phase factor; the low-pass in the grid precision. */
+#define NLSE_LENS_SEGMENTS 8
+typedef struct {
+    double l_dif;          /* cm^2, >= 0 */
+    double w_l;            /* W/cm^2, > 0 */
+    int32_t connectivity;  /* 4 or 8 */
+    int32_t n_re, n_im;    /* segments of the real / imaginary part, 0..8 */
+    int32_t reserved;      /* 0 */
+    double r_re[NLSE_LENS_SEGMENTS], a[NLSE_LENS_SEGMENTS], omega[NLSE_LENS_SEGMENTS],
+        psi[NLSE_LENS_SEGMENTS];
+    double r_im[NLSE_LENS_SEGMENTS], b[NLSE_LENS_SEGMENTS], nu[NLSE_LENS_SEGMENTS],
+        eta[NLSE_LENS_SEGMENTS];
+} nlse_lens;
+
+/* Device scratch the effective lens needs for a grid of these parameters
+ * (256-byte aligned by the caller).  Host-only. */
+nlse_status nlse_lens_scratch_size(const nlse_params* p, size_t* bytes);
+
+/* Apply the effective lens to the current field (steps 1-5 above).
+ *   scratch   caller's device buffer of at least nlse_lens_scratch_size bytes,
+ *             256-byte aligned, overwritten; free again when the call returns.
+ *   count     host int32: the number of lenses.
+ *   centres   NULL, or host int32[capacity]: the centres' row-major indices
+ *             (y*n + x), increasing; the first min(count, capacity) are written.
+ *   w_dif_out NULL, or device memory for n*n reals of the grid precision: w_dif.
+ * The step count and history are kept.  NLSE_EINVAL for a bad argument (joints
+ * not positive and increasing, a coefficient not finite, w_l <= 0, ...);
+ * NLSE_ENOMEM for a scratch smaller than required; NLSE_ESTATE before a field
+ * is loaded.  Synchronises. */
+nlse_status nlse_effective_lens(nlse_grid* g, const nlse_lens* lens, void* scratch, size_t scratch_bytes,
+                                int32_t* count, int32_t* centres, int32_t capacity, void* w_dif_out);
+
 /* Copy up to `capacity` recorded (power, peak) pairs, oldest first, into
  * power[] and peak[] (host arrays; either may be NULL) and their count into
  * *count.  Entry i was recorded after (i+1)*diag_every steps.  The history

@@ -51,6 +51,40 @@ class nlse_batch_tuning(ctypes.Structure):
     ]
 
 
+LENS_SEGMENTS = 8
+
+
+class nlse_lens(ctypes.Structure):
+    _fields_ = [
+        ("l_dif", ctypes.c_double),
+        ("w_l", ctypes.c_double),
+        ("connectivity", ctypes.c_int32),
+        ("n_re", ctypes.c_int32),
+        ("n_im", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ] + [(f, ctypes.c_double * LENS_SEGMENTS) for f in ("r_re", "a", "omega", "psi", "r_im", "b", "nu", "eta")]
+
+
+def make_lens(lens: dict) -> nlse_lens:
+    """Pack an effective-lens dict -- l_dif (cm^2), w_l (W/cm^2), conn (4/8),
+    re = [(r_j, a_j, omega_j, psi_j), ...], im = [(r_l, b_l, nu_l, eta_l), ...]
+    -- into the ABI's record."""
+    q = nlse_lens()
+    q.l_dif = float(lens["l_dif"])
+    q.w_l = float(lens["w_l"])
+    q.connectivity = int(lens.get("conn", 4))
+    for part, names, cnt in (("re", ("r_re", "a", "omega", "psi"), "n_re"),
+                             ("im", ("r_im", "b", "nu", "eta"), "n_im")):
+        segs = lens.get(part, ())
+        if len(segs) > LENS_SEGMENTS:
+            raise ValueError(f"at most {LENS_SEGMENTS} segments per part")
+        setattr(q, cnt, len(segs))
+        for j, seg in enumerate(segs):
+            for f, v in zip(names, seg):
+                getattr(q, f)[j] = float(v)
+    return q
+
+
 class NlseError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = int(status)
@@ -80,6 +114,10 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "nlse_turbulent_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double]),
+    "nlse_lens_scratch_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "nlse_effective_lens": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_void_p]),
     "nlse_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]),
     "nlse_device_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -214,6 +252,21 @@ def nlse_hot_areas(h, w_p: float, connectivity: int, labels_ptr: int, on_device:
 def nlse_turbulent_screen(h, xi_ptr: int, on_device: bool, tau: float, k_h: float, thickness: float) -> None:
     check(lib().nlse_turbulent_screen(h, ctypes.c_void_p(xi_ptr), int(bool(on_device)), float(tau), float(k_h),
                                       float(thickness)), "nlse_turbulent_screen")
+
+
+def nlse_lens_scratch_size(p: nlse_params) -> int:
+    b = ctypes.c_size_t(0)
+    check(lib().nlse_lens_scratch_size(ctypes.byref(p), ctypes.byref(b)), "nlse_lens_scratch_size")
+    return int(b.value)
+
+
+def nlse_effective_lens(h, lens: nlse_lens, scratch: int, scratch_bytes: int, centres_ptr: int, capacity: int,
+                        w_dif_ptr: int) -> int:
+    c = ctypes.c_int32(0)
+    check(lib().nlse_effective_lens(h, ctypes.byref(lens), ctypes.c_void_p(scratch), int(scratch_bytes),
+                                    ctypes.byref(c), ctypes.c_void_p(centres_ptr or None), int(capacity),
+                                    ctypes.c_void_p(w_dif_ptr or None)), "nlse_effective_lens")
+    return int(c.value)
 
 
 def nlse_history(h, power_ptr: int, peak_ptr: int, capacity: int) -> int:

@@ -16,6 +16,7 @@
 #include "../../include/nlse.h"
 #include "dispatch.cuh"
 #include "hot_areas.cuh"
+#include "lens.cuh"
 #include "host_detail.h"
 
 using namespace nlse;
@@ -490,6 +491,130 @@ cudaError_t finalize(const double* partials, int nparts, double scale, double* o
 
 // ------------------------------------------------------------------ C ABI --
 
+namespace {
+
+// scratch of the effective lens: counters, complex work array (w, its
+// spectrum, w_dif), labels, per-root maximum keys (then the centre list),
+// per-root centres
+struct LensScratch {
+    size_t ctr, wbuf, lab, key, cen, total;
+};
+
+LensScratch lens_scratch_layout(int n, int precision) {
+    const size_t nn = (size_t)n * n;
+    LensScratch L;
+    size_t o = 0;
+    L.ctr = o;  o = align256(o + 2 * sizeof(int));
+    L.wbuf = o; o = align256(o + nn * (precision == NLSE_FP64 ? 16 : 8));
+    L.lab = o;  o = align256(o + nn * sizeof(int));
+    L.key = o;  o = align256(o + nn * sizeof(unsigned long long));
+    L.cen = o;  o = align256(o + nn * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+bool lens_part_ok(int count, const double* r, const double* amp, const double* freq, const double* phase) {
+    if (count < 0 || count > NLSE_LENS_SEGMENTS) return false;
+    double prev = 0.0;
+    for (int j = 0; j < count; ++j) {
+        if (!std::isfinite(r[j]) || !(r[j] > prev)) return false;
+        if (!std::isfinite(amp[j]) || !std::isfinite(freq[j]) || !std::isfinite(phase[j])) return false;
+        prev = r[j];
+    }
+    return true;
+}
+
+template <typename T>
+nlse_status lens_impl(nlse_grid* g, const nlse_lens* ls, unsigned char* sc, int32_t* count, int32_t* centres,
+                      int32_t capacity, T* w_dif_out) {
+    using V = VT<T>;
+    const KernelSet<T>* ks = Sel<T>::ks(g);
+    const int n = g->p.n;
+    const size_t nn = (size_t)n * n;
+    const LensScratch SL = lens_scratch_layout(n, g->p.precision);
+    int* ctr = reinterpret_cast<int*>(sc + SL.ctr);
+    V* wbuf = reinterpret_cast<V*>(sc + SL.wbuf);
+    int* lab = reinterpret_cast<int*>(sc + SL.lab);
+    unsigned long long* key = reinterpret_cast<unsigned long long*>(sc + SL.key);
+    int* cen = reinterpret_cast<int*>(sc + SL.cen);
+    int* list = reinterpret_cast<int*>(sc + SL.key);  // the keys are done with when the list is gathered
+    V* field = at<T>(g, g->lay.aux);
+    const auto* tw = twiddles_fixed<T>(g->ws + g->lay.tw);
+    cudaStream_t st = g->stream;
+    const int blocks = (int)std::min<size_t>((nn + 255) / 256, 152 * 8);
+
+    // the field leaves the state for the scratch half of the grid (row-major,
+    // global phase removed) and comes back after the screen
+    nlse_status s = readout_any(g, field, nullptr);
+    if (s != NLSE_OK) return s;
+    if (cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st) != cudaSuccess) return NLSE_ECUDA;
+    k_lens_fluence<T><<<blocks, 256, 0, st>>>(field, wbuf, nn);
+    cudaError_t e = ks->dft2(wbuf, tw, false, st);
+    if (e != cudaSuccess) return NLSE_ECUDA;
+    k_lens_filter<T><<<blocks, 256, 0, st>>>(wbuf, n, kTwoPi / g->p.L, ls->l_dif);
+    e = ks->dft2(wbuf, tw, true, st);
+    if (e != cudaSuccess) return NLSE_ECUDA;
+
+    // lenses: regions of Re(wbuf) >= w_l, labelled by their smallest index
+    const int rt = n < 256 ? n : 256;
+    k_hot_runs<T><<<n, rt, 0, st>>>(reinterpret_cast<const T*>(wbuf), n, 2, (T)ls->w_l, lab);
+    k_hot_merge<<<blocks, 256, 0, st>>>(lab, n, ls->connectivity, ctr + 1);
+    k_hot_roots<<<blocks, 256, 0, st>>>(lab, n, ctr);
+    k_hot_spread<<<blocks, 256, 0, st>>>(lab, (int)nn);
+    // centres: per lens the smallest index of its largest value
+    if (cudaMemsetAsync(key, 0, nn * sizeof(unsigned long long), st) != cudaSuccess) return NLSE_ECUDA;
+    if (cudaMemsetAsync(cen, 0x7f, nn * sizeof(int), st) != cudaSuccess) return NLSE_ECUDA;
+    k_lens_keymax<T><<<blocks, 256, 0, st>>>(wbuf, lab, key, nn);
+    k_lens_argmax<T><<<blocks, 256, 0, st>>>(wbuf, lab, key, cen, nn);
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    int hc[2] = {0, 0};
+    if (cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NLSE_ECUDA;
+    if (cudaMemsetAsync(ctr, 0, sizeof(int), st) != cudaSuccess) return NLSE_ECUDA;
+    k_lens_gather<<<blocks, 256, 0, st>>>(lab, cen, list, ctr, nn);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return NLSE_ECUDA;
+    if (hc[1] & kHotStatusGaveUp) return NLSE_ETIMEOUT;
+    const int nl = hc[0];
+    // the list in increasing index order: the order the screen sums the lenses in
+    std::vector<int32_t> hl((size_t)nl);
+    if (nl > 0) {
+        if (cudaMemcpyAsync(hl.data(), list, (size_t)nl * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return NLSE_ECUDA;
+        std::sort(hl.begin(), hl.end());
+        if (cudaMemcpyAsync(list, hl.data(), (size_t)nl * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return NLSE_ECUDA;
+    }
+    if (w_dif_out) k_lens_real<T><<<blocks, 256, 0, st>>>(wbuf, w_dif_out, nn);
+
+    // Eqs. 5-6 and the screen of Eq. 2
+    const double dx = g->p.L / n;
+    LensCoef c;
+    c.n_re = ls->n_re;
+    c.n_im = ls->n_im;
+    double reach = 0.0;
+    for (int j = 0; j < kLensSeg; ++j) {
+        c.r_re[j] = ls->r_re[j]; c.a[j] = ls->a[j]; c.omega[j] = ls->omega[j]; c.psi[j] = ls->psi[j];
+        c.r_im[j] = ls->r_im[j]; c.b[j] = ls->b[j]; c.nu[j] = ls->nu[j]; c.eta[j] = ls->eta[j];
+    }
+    if (ls->n_re > 0) reach = std::max(reach, ls->r_re[ls->n_re - 1]);
+    if (ls->n_im > 0) reach = std::max(reach, ls->r_im[ls->n_im - 1]);
+    c.reach2 = (reach / dx + 1.0) * (reach / dx + 1.0);
+    if (nl > 0 && (ls->n_re > 0 || ls->n_im > 0)) {
+        const int ts = n < 16 ? n : 16;
+        k_lens_apply<T><<<dim3(n / ts, n / ts), dim3(ts, ts), 0, st>>>(field, n, dx, list, nl, c);
+    }
+    e = ks->row_forward(field, at<T>(g, g->lay.state), tw, st);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    g->theta = 0.0;  // the readout removed the accumulated global phase
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NLSE_ECUDA;
+    *count = nl;
+    if (centres)
+        for (int i = 0; i < nl && i < capacity; ++i) centres[i] = hl[(size_t)i];
+    return NLSE_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* nlse_status_string(nlse_status s) {
@@ -732,8 +857,8 @@ nlse_status nlse_hot_areas(nlse_grid* g, double w_p, int32_t connectivity, int32
     int* word = reinterpret_cast<int*>(dat(g, g->lay.partials));
     if (cudaMemsetAsync(word, 0, 2 * sizeof(int), g->stream) != cudaSuccess) return NLSE_ECUDA;
     const int rt = n < 256 ? n : 256;
-    if (f64) k_hot_runs<double><<<n, rt, 0, g->stream>>>((const double*)flu, n, w_p, lab);
-    else k_hot_runs<float><<<n, rt, 0, g->stream>>>((const float*)flu, n, (float)w_p, lab);
+    if (f64) k_hot_runs<double><<<n, rt, 0, g->stream>>>((const double*)flu, n, 1, w_p, lab);
+    else k_hot_runs<float><<<n, rt, 0, g->stream>>>((const float*)flu, n, 1, (float)w_p, lab);
     const int blocks = std::min((nn + 255) / 256, 152 * 8);
     k_hot_merge<<<blocks, 256, 0, g->stream>>>(lab, n, connectivity, word + 1);
     k_hot_roots<<<blocks, 256, 0, g->stream>>>(lab, n, word);
@@ -778,7 +903,7 @@ nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device
     cudaError_t e;
     if (f64) {
         k_turb_spectrum<double><<<blocks, 256, 0, g->stream>>>((const double2*)src, (double2*)spec, n, tau, r2);
-        e = g->k64->idft2((double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw), g->stream);
+        e = g->k64->dft2((double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw), true, g->stream);
         if (e == cudaSuccess) {
             k_turb_apply<double><<<blocks, 256, 0, g->stream>>>((double2*)field, (const double2*)spec, c, nn);
             e = g->k64->row_forward((const double2*)field, (double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw),
@@ -786,7 +911,7 @@ nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device
         }
     } else {
         k_turb_spectrum<float><<<blocks, 256, 0, g->stream>>>((const float2*)src, (float2*)spec, n, tau, r2);
-        e = g->k32->idft2((float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw), g->stream);
+        e = g->k32->dft2((float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw), true, g->stream);
         if (e == cudaSuccess) {
             k_turb_apply<float><<<blocks, 256, 0, g->stream>>>((float2*)field, (const float2*)spec, c, nn);
             e = g->k32->row_forward((const float2*)field, (float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw),
@@ -796,6 +921,33 @@ nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
     g->theta = 0.0;  // the readout removed the accumulated global phase
     return NLSE_OK;
+}
+
+
+nlse_status nlse_lens_scratch_size(const nlse_params* p, size_t* bytes) {
+    if (!bytes) return NLSE_EINVAL;
+    nlse_status s = validate(p);
+    if (s != NLSE_OK) return s;
+    *bytes = lens_scratch_layout(p->n, p->precision).total;
+    return NLSE_OK;
+}
+
+nlse_status nlse_effective_lens(nlse_grid* g, const nlse_lens* lens, void* scratch, size_t scratch_bytes,
+                                int32_t* count, int32_t* centres, int32_t capacity, void* w_dif_out) {
+    if (!g || !lens || !scratch || !count || (centres && capacity < 0)) return NLSE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(scratch) & 255) return NLSE_EINVAL;
+    if (!std::isfinite(lens->l_dif) || lens->l_dif < 0.0 || !std::isfinite(lens->w_l) || !(lens->w_l > 0.0))
+        return NLSE_EINVAL;
+    if ((lens->connectivity != 4 && lens->connectivity != 8) || lens->reserved != 0) return NLSE_EINVAL;
+    if (!lens_part_ok(lens->n_re, lens->r_re, lens->a, lens->omega, lens->psi) ||
+        !lens_part_ok(lens->n_im, lens->r_im, lens->b, lens->nu, lens->eta))
+        return NLSE_EINVAL;
+    if (scratch_bytes < lens_scratch_layout(g->p.n, g->p.precision).total) return NLSE_ENOMEM;
+    if (!g->loaded) return NLSE_ESTATE;
+    unsigned char* sc = static_cast<unsigned char*>(scratch);
+    if (g->p.precision == NLSE_FP64)
+        return lens_impl<double>(g, lens, sc, count, centres, capacity, static_cast<double*>(w_dif_out));
+    return lens_impl<float>(g, lens, sc, count, centres, capacity, static_cast<float*>(w_dif_out));
 }
 
 nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capacity, int32_t* count) {

@@ -39,8 +39,8 @@ template <typename T> struct KernelSet {
     cudaError_t (*loss_seed)(const V* state, V* gam, const double* target, const W* tw,
                              double seed_scale, double* partials, cudaStream_t s);
     cudaError_t (*adj_row)(V* gam, const V* tn, const W* tw, AdjCoef<T> ac, double* acc, cudaStream_t s);
-    // unnormalised inverse 2D DFT of a row-major array, in place
-    cudaError_t (*idft2)(V* data, const W* tw, cudaStream_t s);
+    // unnormalised 2D DFT (inverse: conjugate kernel) of a row-major array, in place
+    cudaError_t (*dft2)(V* data, const W* tw, bool inverse, cudaStream_t s);
 };
 
 // Raise the dynamic shared-memory limit of one kernel once per device.  The
@@ -185,16 +185,22 @@ cudaError_t launch_row_forward(const typename vec2<T>::type* src, typename vec2<
     return cudaGetLastError();
 }
 
-template <typename T, int N>
-cudaError_t launch_idft2(typename vec2<T>::type* data, const typename tab_of<T>::type* tw, cudaStream_t s) {
+template <typename T, int N, bool INV>
+cudaError_t launch_dft2_dir(typename vec2<T>::type* data, const typename tab_of<T>::type* tw, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
-    cudaError_t e = ensure_smem<k_idft_lines<T, N, false>>(SMEM);
-    if (e == cudaSuccess) e = ensure_smem<k_idft_lines<T, N, true>>(SMEM);
+    cudaError_t e = ensure_smem<k_dft_lines<T, N, false, INV>>(SMEM);
+    if (e == cudaSuccess) e = ensure_smem<k_dft_lines<T, N, true, INV>>(SMEM);
     if (e != cudaSuccess) return e;
-    k_idft_lines<T, N, false><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
-    k_idft_lines<T, N, true><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
+    k_dft_lines<T, N, false, INV><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
+    k_dft_lines<T, N, true, INV><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
     return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t launch_dft2(typename vec2<T>::type* data, const typename tab_of<T>::type* tw, bool inverse,
+                        cudaStream_t s) {
+    return inverse ? launch_dft2_dir<T, N, true>(data, tw, s) : launch_dft2_dir<T, N, false>(data, tw, s);
 }
 
 template <typename T, int N>
@@ -276,7 +282,7 @@ template <typename T, int N> KernelSet<T> make_set() {
     k.readout = &launch_readout<T, N>;
     k.loss_seed = &launch_loss_seed<T, N>;
     k.adj_row = &launch_adj_row<T, N>;
-    k.idft2 = &launch_idft2<T, N>;
+    k.dft2 = &launch_dft2<T, N>;
     return k;
 }
 

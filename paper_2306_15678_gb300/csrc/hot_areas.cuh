@@ -27,24 +27,27 @@ namespace nlse {
 constexpr int kHotUnionTries = 1 << 20;  // bound on the retries of one union (never reached)
 constexpr int kHotStatusGaveUp = 1;      // bit of the per-call status word
 
-// 1. runs: blockDim = min(n, 256) threads, each over n / blockDim contiguous pixels
+// 1. runs: blockDim = min(n, 256) threads, each over n / blockDim contiguous
+// pixels; pixel (y, x) of the row-major input is w[(y n + x) stride] (stride 2
+// reads the real parts of a complex array)
 template <typename T>
-__global__ void __launch_bounds__(256) k_hot_runs(const T* __restrict__ w, int n, T wp, int* __restrict__ label) {
+__global__ void __launch_bounds__(256) k_hot_runs(const T* __restrict__ w, int n, int stride, T wp,
+                                                  int* __restrict__ label) {
     __shared__ int warp_last[8];
     const int y = blockIdx.x;
     const int E = n / blockDim.x;
-    const T* row = w + (size_t)y * n;
+    const T* row = w + (size_t)y * n * stride;
     int* lrow = label + (size_t)y * n;
     const int x0 = threadIdx.x * E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
 
     // the last run start inside this thread's pixels
-    const bool left_on = x0 > 0 && row[x0 - 1] >= wp;
+    const bool left_on = x0 > 0 && row[(size_t)(x0 - 1) * stride] >= wp;
     int last = -1;
     bool prev = left_on;
     for (int k = 0; k < E; ++k) {
-        const bool on = row[x0 + k] >= wp;
+        const bool on = row[(size_t)(x0 + k) * stride] >= wp;
         if (on && !prev) last = x0 + k;
         prev = on;
     }
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(256) k_hot_runs(const T* __restrict__ w, int n
 
     prev = left_on;
     for (int k = 0; k < E; ++k) {
-        const bool on = row[x0 + k] >= wp;
+        const bool on = row[(size_t)(x0 + k) * stride] >= wp;
         if (on && !prev) cur = x0 + k;
         lrow[x0 + k] = on ? y * n + cur : -1;
         prev = on;

@@ -1,7 +1,7 @@
 // turbulence.cuh -- kernels of the turbulent layer (arXiv 2306.15678, Sec. 3.3,
-// Eqs. 9-10): the step spectrum of the random screen, the unnormalised inverse
-// 2D DFT that turns it into the permittivity screen eps_t, and the layer's
-// phase factor exp(-i thickness eps_t / (2 k0)) on the row-major field.
+// Eqs. 9-10): the step spectrum of the random screen, the unnormalised 2D DFT
+// of row-major arrays (also used by the effective lens), and the layer's phase
+// factor exp(-i thickness eps_t / (2 k0)) on the row-major field.
 #pragma once
 #include "kernels.cuh"
 
@@ -24,14 +24,14 @@ __global__ void k_turb_spectrum(const typename vec2<T>::type* xi, typename vec2<
     }
 }
 
-// Unnormalised inverse DFT of every line of a row-major n x n array, in place:
-// rows (along x) when COLS is false, columns (along y) when true.  Every line
-// is loaded before the first exchange barrier and stored after the last, so
-// the transform may overwrite its input.
-template <typename T, int N, bool COLS>
+// Unnormalised DFT (forward, or inverse when INV) of every line of a row-major
+// n x n array, in place: rows (along x) when COLS is false, columns (along y)
+// when true.  Every line is loaded before the first exchange barrier and
+// stored after the last, so the transform may overwrite its input.
+template <typename T, int N, bool COLS, bool INV>
 __global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
                                   min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
-k_idft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __restrict__ tw) {
+k_dft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __restrict__ tw) {
     using V = typename vec2<T>::type;
     constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
     constexpr int LS = line_stride<T, N, RPB>();
@@ -43,7 +43,7 @@ k_idft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __res
     V v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = data[base + (size_t)(j + m * TL) * stride];
-    fft_stockham<V, N, E, true>(v, smem + g * LS, tw, j);
+    fft_stockham<V, N, E, INV>(v, smem + g * LS, tw, j);
 #pragma unroll
     for (int m = 0; m < E; ++m) data[base + (size_t)(j + m * TL) * stride] = v[m];
 }

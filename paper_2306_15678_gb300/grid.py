@@ -136,6 +136,20 @@ class Grid:
             capi.nlse_turbulent_screen(self.h, a.ctypes.data, False, tau, k_h, thickness)
         return self
 
+    def effective_lens(self, lens: dict, w_dif: bool = False):
+        """Effective-lens screen of Eqs. 4-6 on the current field (see
+        capi.make_lens for the dict).  Returns (count, centres as row-major
+        int32 indices, w_dif as a device tensor or None)."""
+        need = capi.nlse_lens_scratch_size(self.params)
+        if getattr(self, "_lens_scratch", None) is None or self._lens_scratch.numel() < need:
+            self._lens_scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+        cap = self.n * self.n
+        cent = np.empty(cap, dtype=np.int32)
+        wd = torch.empty((self.n, self.n), dtype=self.trdtype, device=self.device) if w_dif else None
+        k = capi.nlse_effective_lens(self.h, capi.make_lens(lens), self._lens_scratch.data_ptr(), need,
+                                     cent.ctypes.data, cap, wd.data_ptr() if wd is not None else 0)
+        return k, cent[:k].copy(), wd
+
     def history(self):
         cap = 4096
         pw = np.empty(cap)

@@ -101,3 +101,25 @@ def test_symmetric_steps_only_for_single_grids():
     assert ei.value.status == capi.NLSE_EUNSUPPORTED
     with pytest.raises(ValueError):
         make_params(dict(cfg, scheme="leapfrog"))
+
+
+def test_lens_scratch_size_and_null_checks():
+    """The effective lens's scratch: counters, a complex work array, labels,
+    64-bit keys and centres per point; host-only, validates the parameters."""
+    cfg = configs.cfg_dense_fp32()
+    p = make_params(cfg)
+    n = p.n
+    assert capi.nlse_lens_scratch_size(p) >= n * n * (8 + 4 + 8 + 4)
+    p64 = make_params(cfg, precision="fp64")
+    assert capi.nlse_lens_scratch_size(p64) >= n * n * (16 + 4 + 8 + 4)
+    q = make_params(cfg)
+    q.n = 100
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_lens_scratch_size(q)
+    assert ei.value.status == capi.NLSE_EINVAL
+    lens = capi.make_lens(dict(l_dif=1e-4, w_l=1e11, re=[(0.1, 1.0, 1.0, 0.0)]))
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_effective_lens(None, lens, 0, 0, 0, 0, 0)
+    assert ei.value.status == capi.NLSE_EINVAL
+    with pytest.raises(ValueError):
+        capi.make_lens(dict(l_dif=0.0, w_l=1.0, re=[(0.1 * (j + 1), 1, 1, 0) for j in range(9)]))
