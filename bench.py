@@ -450,6 +450,32 @@ def main():
                    "steps_marched": g.steps_taken,
                    "includes": "fluence readout, run labelling, union-find merge, roots, spread; count to host"}
 
+        # ---- effective lens (Eqs. 4-6) and a turbulent layer (Eqs. 9-10) on the marched field
+        lens_t = None
+        if not args.no_hot:
+            lens = dict(l_dif=4e-4, w_l=1e12, conn=4,
+                        re=[(0.03, 0.9, 40.0, 0.2), (0.06, -0.5, 30.0, 1.0), (0.1, 0.2, 20.0, -0.4)],
+                        im=[(0.04, 0.3, 35.0, 0.1), (0.08, 0.1, 15.0, 0.5)])
+            xi = torch.from_numpy(beams.turbulence_draws(n, 77).astype(np.complex64)).to(dev)
+            tl, tt = [], []
+            for _ in range(3):
+                h0 = torch.cuda.Event(enable_timing=True)
+                h1 = torch.cuda.Event(enable_timing=True)
+                h0.record(stream)
+                nlens, _, _ = g.effective_lens(lens)
+                h1.record(stream)
+                torch.cuda.synchronize(dev)
+                tl.append(h0.elapsed_time(h1))
+                h0.record(stream)
+                g.turbulent_screen(xi, 1e-3, 2 * math.pi / cfg["L"] * 40.0, 50.0)
+                h1.record(stream)
+                torch.cuda.synchronize(dev)
+                tt.append(h0.elapsed_time(h1))
+            lens_t = {"effective_lens_ms": min(tl), "lenses": nlens, "w_l_w_per_cm2": lens["w_l"],
+                      "l_dif_cm2": lens["l_dif"], "turbulent_layer_ms": min(tt),
+                      "includes": "lens: readout, low-pass DFT pair, labelling, centres, ansatz sum, reload; "
+                                  "layer: readout, spectrum, inverse DFT pair, phase, reload"}
+
         # ---- symmetric (Strang) steps on the same field: one more screen per row pass
         strang = None
         if not args.no_strang:
@@ -528,7 +554,7 @@ def main():
             "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
-            "strang": strang, "hot_areas": hot, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
+            "strang": strang, "hot_areas": hot, "lens_and_turbulence": lens_t, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
