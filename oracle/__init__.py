@@ -121,6 +121,8 @@ def _configure(lib):
     lib.orc_power.argtypes = [cp, ctypes.c_int, ctypes.c_double]
     lib.orc_power.restype = ctypes.c_double
     lib.orc_peak.argtypes = [cp, ctypes.c_int]
+    lib.orc_moment.argtypes = [cp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.orc_moment.restype = ctypes.c_double
     lib.orc_peak.restype = ctypes.c_double
     lib.orc_fluence.argtypes = [cp, ctypes.c_int, ctypes.c_int, cp]
     lib.orc_loss.argtypes = [cp, cp, ctypes.c_int]
@@ -229,6 +231,12 @@ def power(U, L: float) -> float:
 def peak(U) -> float:
     U = _c128(U)
     return float(_load().orc_peak(U.ctypes.data, U.shape[0]))
+
+
+def moment(U, L: float, p: int, q: int) -> float:
+    """Eq. 8 moment M(p, q) = int I^p (x^2 + y^2)^q dx dy (cell-centred grid)."""
+    U = _c128(U)
+    return float(_load().orc_moment(U.ctypes.data, U.shape[0], float(L), int(p), int(q)))
 
 
 def fluence(U, ds: int = 1) -> np.ndarray:

@@ -298,6 +298,26 @@ double orc_power(const cplx *U, int n, double L) {
     return nsum_abs2(U, (size_t)n * n) * dx * dx;
 }
 
+/* Spatial moment of Eq. 8, M(p, q) = integral of I^p (x^2 + y^2)^q dx dy with
+ * I = U U*, by the rectangle rule on the cell centres x_j = (j - n/2 + 1/2) dx.
+ * The printed Q^{mn} = int (U_n U_n*)^{2m} (x^2+y^2)^m is read, as Eq. 3's
+ * exponents are, with (UU*)^{2m} standing for |U|^{2m} = I^m: Q^m = M(m, m)
+ * for beam n.  M(1, 0) is the power. */
+double orc_moment(const cplx *U, int n, double L, int p, int q) {
+    double dx = L / (double)n;
+    double sum = 0.0;
+    for (int y = 0; y < n; ++y) {
+        double yc = ((double)y - n / 2 + 0.5) * dx;
+        for (int x = 0; x < n; ++x) {
+            double xc = ((double)x - n / 2 + 0.5) * dx;
+            cplx u = U[(size_t)y * n + x];
+            double inten = creal(u) * creal(u) + cimag(u) * cimag(u);
+            sum += pow(inten, (double)p) * pow(xc * xc + yc * yc, (double)q);
+        }
+    }
+    return sum * dx * dx;
+}
+
 /* peak intensity max |U|^2, W/cm^2 */
 double orc_peak(const cplx *U, int n) {
     double m = 0.0;

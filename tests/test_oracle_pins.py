@@ -538,6 +538,28 @@ def test_turbulent_layer_acts_like_the_kerr_term():
     assert rel_max(U, oracle.screen(v, cfg)) < 1e-10
 
 
+# ------------------------------------------------ moments (Eq. 8)
+
+def test_moments_gaussian_closed_form():
+    """Eq. 8 moments of a Gaussian beam I = I0 exp(-2 r^2/w0^2), centred on the
+    window: int I^p r^{2q} = I0^p pi q! (w0^2 / (2 p))^(q+1) (the rectangle rule
+    on the cell centres is exact to rounding for a resolved Gaussian); M(1, 0)
+    is the power."""
+    n, L, w0 = 128, 1.28, 0.12
+    c = beams.cell_centres(n, L)
+    X, Y = np.meshgrid(c, c)
+    I0 = 3e11
+    U = np.sqrt(I0) * np.exp(-(X ** 2 + Y ** 2) / w0 ** 2) * np.exp(0.7j)
+    for p, q in [(1, 0), (1, 1), (2, 0), (2, 2), (3, 1), (1, 3)]:
+        expect = I0 ** p * math.pi * math.factorial(q) * (w0 ** 2 / (2 * p)) ** (q + 1)
+        assert abs(oracle.moment(U, L, p, q) / expect - 1) < 1e-12, (p, q)
+    assert abs(oracle.moment(U, L, 1, 0) / oracle.power(U, L) - 1) < 1e-14
+    # off-centre beam: the moment is taken about the window centre (parallel-axis rule)
+    Us = np.sqrt(I0) * np.exp(-((X - 0.2) ** 2 + Y ** 2) / w0 ** 2)
+    expect = I0 * math.pi * w0 ** 2 / 2 * (w0 ** 2 / 2 + 0.2 ** 2)
+    assert abs(oracle.moment(Us, L, 1, 1) / expect - 1) < 1e-12
+
+
 # ------------------------------------------- effective lens (Eqs. 4-6)
 
 def test_lens_lowpass_gaussian_closed_form():
@@ -670,6 +692,10 @@ MUTANTS = [
      "S[(size_t)q * n + c] = (m2 > r2) ?", "turb_line"),
     ("turbulent screen without the n^2 of the unnormalised sum", "eps[i] = creal(S[i]) * (double)nn;",
      "eps[i] = creal(S[i]);", "turb_line"),
+    ("moment about the window corner", "double xc = ((double)x - n / 2 + 0.5) * dx;",
+     "double xc = ((double)x) * dx;", "moments"),
+    ("moment radius exponent q instead of 2q", "pow(xc * xc + yc * yc, (double)q)",
+     "pow(sqrt(xc * xc + yc * yc), (double)q)", "moments"),
     ("low-pass sign", "W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx + ky * ky));",
      "W[(size_t)r * n + c] *= exp(l_dif * (kx * kx + ky * ky));", "lens_gauss"),
     ("low-pass along x only", "W[(size_t)r * n + c] *= exp(-l_dif * (kx * kx + ky * ky));",
@@ -707,6 +733,7 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "lens_centres": test_lens_centres_hand_made,
         "lens_value": test_lens_value_is_piecewise_eq6,
         "lens_apply": test_lens_apply_closed_form_and_superposition,
+        "moments": test_moments_gaussian_closed_form,
     }
     with pytest.raises(AssertionError):
         pins[pin]()
