@@ -268,6 +268,14 @@ nlse_status nlse_lens_scratch_size(const nlse_params* p, size_t* bytes);
 nlse_status nlse_effective_lens(nlse_grid* g, const nlse_lens* lens, void* scratch, size_t scratch_bytes,
                                 int32_t* count, int32_t* centres, int32_t capacity, void* w_dif_out);
 
+/* Spatial moments of the current fluence (Eq. 8, the moment measure of the
+ * fit): out[k] = sum over the grid of I^p[k] (x^2 + y^2)^q[k] dx^2, I = U U*,
+ * on the cell centres x_j = (j - n/2 + 1/2) dx, y likewise (the window centre
+ * is the origin).  Eq. 8's Q^m of a beam is M(m, m) (its (UU*)^{2m} read as
+ * I^m); M(1, 0) is the power.  count = 1..8, 1 <= p <= 16, 0 <= q <= 16
+ * (NLSE_EINVAL otherwise); FP64 sums in a fixed order.  Synchronises. */
+nlse_status nlse_moments(nlse_grid* g, int32_t count, const int32_t* p, const int32_t* q, double* out);
+
 /* Copy up to `capacity` recorded (power, peak) pairs, oldest first, into
  * power[] and peak[] (host arrays; either may be NULL) and their count into
  * *count.  Entry i was recorded after (i+1)*diag_every steps.  The history

@@ -79,3 +79,24 @@ def turbulence_draws(n: int, seed: int) -> np.ndarray:
     PCG64, given seed), in FFT bin order."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))
     return (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * math.sqrt(0.5)
+
+
+def ga_draws(seed: int, count: int) -> np.ndarray:
+    """The uniform [0, 1) draws a genetic search consumes, in order (NumPy
+    PCG64, given seed): gene sampling, roulette picks, crossover and mutation
+    all read this one stream, so that two implementations of the search given
+    the same stream make the same choices."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    return rng.random(int(count))
+
+
+def fit_beam_set(n: int = 256, count: int = 2) -> list:
+    """Eq. 7 test beams of the fit: Gaussian beams U_n = A_n exp(-(r/r_n)^2)
+    spanning the paper's range (P from 3 to 9 P_cr, r_n from 0.5 to 2.5 mm),
+    each on a window of 8 r_n: a list of (r_n in cm, P / P_cr, L in cm)."""
+    out = []
+    for i in range(count):
+        t = i / max(count - 1, 1)
+        r = 0.05 + t * (0.25 - 0.05)
+        out.append((r, 3.0 + 6.0 * t, 8.0 * r))
+    return out

@@ -115,6 +115,8 @@ _SIGS = {
     "nlse_turbulent_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double]),
     "nlse_lens_scratch_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "nlse_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "nlse_effective_lens": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_void_p]),
@@ -252,6 +254,16 @@ def nlse_hot_areas(h, w_p: float, connectivity: int, labels_ptr: int, on_device:
 def nlse_turbulent_screen(h, xi_ptr: int, on_device: bool, tau: float, k_h: float, thickness: float) -> None:
     check(lib().nlse_turbulent_screen(h, ctypes.c_void_p(xi_ptr), int(bool(on_device)), float(tau), float(k_h),
                                       float(thickness)), "nlse_turbulent_screen")
+
+
+def nlse_moments(h, pq) -> list:
+    """Eq. 8 moments M(p, q) for the (p, q) pairs in pq."""
+    k = len(pq)
+    P = (ctypes.c_int32 * max(k, 1))(*[int(a) for a, _ in pq])
+    Q = (ctypes.c_int32 * max(k, 1))(*[int(b) for _, b in pq])
+    out = (ctypes.c_double * max(k, 1))()
+    check(lib().nlse_moments(h, k, P, Q, out), "nlse_moments")
+    return [float(out[i]) for i in range(k)]
 
 
 def nlse_lens_scratch_size(p: nlse_params) -> int:

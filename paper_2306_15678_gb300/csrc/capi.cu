@@ -17,6 +17,7 @@
 #include "dispatch.cuh"
 #include "hot_areas.cuh"
 #include "lens.cuh"
+#include "moments.cuh"
 #include "host_detail.h"
 
 using namespace nlse;
@@ -493,11 +494,11 @@ cudaError_t finalize(const double* partials, int nparts, double scale, double* o
 
 namespace {
 
-// scratch of the effective lens: counters, complex work array (w, its
-// spectrum, w_dif), labels, per-root maximum keys (then the centre list),
-// per-root centres
+// scratch of the effective lens: counters, the separable low-pass factors,
+// complex work array (w, its spectrum, w_dif), labels, per-root maximum keys
+// (then the centre list), per-root centres
 struct LensScratch {
-    size_t ctr, wbuf, lab, key, cen, total;
+    size_t ctr, tab, wbuf, lab, key, cen, total;
 };
 
 LensScratch lens_scratch_layout(int n, int precision) {
@@ -505,6 +506,7 @@ LensScratch lens_scratch_layout(int n, int precision) {
     LensScratch L;
     size_t o = 0;
     L.ctr = o;  o = align256(o + 2 * sizeof(int));
+    L.tab = o;  o = align256(o + 2 * (size_t)n * sizeof(double));
     L.wbuf = o; o = align256(o + nn * (precision == NLSE_FP64 ? 16 : 8));
     L.lab = o;  o = align256(o + nn * sizeof(int));
     L.key = o;  o = align256(o + nn * sizeof(unsigned long long));
@@ -549,9 +551,21 @@ nlse_status lens_impl(nlse_grid* g, const nlse_lens* ls, unsigned char* sc, int3
     if (s != NLSE_OK) return s;
     if (cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st) != cudaSuccess) return NLSE_ECUDA;
     k_lens_fluence<T><<<blocks, 256, 0, st>>>(field, wbuf, nn);
+    // separable low-pass factors: fx[p] = exp(-l_dif kx_p^2), fy[q] = exp(-l_dif ky_q^2) / n^2
+    std::vector<T> htab(2 * (size_t)n);
+    const double kunit = kTwoPi / g->p.L;
+    for (int m = 0; m < n; ++m) {
+        const double k = kunit * (m < n / 2 ? m : m - n);
+        const double f = std::exp(-ls->l_dif * k * k);
+        htab[m] = (T)f;
+        htab[n + m] = (T)(f / ((double)n * n));
+    }
+    T* tab = reinterpret_cast<T*>(sc + SL.tab);
+    if (cudaMemcpyAsync(tab, htab.data(), htab.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return NLSE_ECUDA;
     cudaError_t e = ks->dft2(wbuf, tw, false, st);
     if (e != cudaSuccess) return NLSE_ECUDA;
-    k_lens_filter<T><<<blocks, 256, 0, st>>>(wbuf, n, kTwoPi / g->p.L, ls->l_dif);
+    k_lens_filter<T><<<blocks, 256, 0, st>>>(wbuf, n, tab, tab + n);
     e = ks->dft2(wbuf, tw, true, st);
     if (e != cudaSuccess) return NLSE_ECUDA;
 
@@ -898,11 +912,13 @@ nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device
     }
     const double rc = k_h * g->p.L / kTwoPi;
     const double r2 = rc * rc;
+    // largest integer p~^2 + q~^2 inside the cut-off (none above 2 (n/2)^2)
+    const long long m2max = r2 >= 2.0 * (double)(n / 2) * (n / 2) ? 2LL * (n / 2) * (n / 2) : (long long)std::floor(r2);
     const double c = thickness / (2.0 * (kTwoPi * g->p.n0 / g->p.lambda0));
     const int blocks = (int)std::min<size_t>((nn + 255) / 256, 152 * 8);
     cudaError_t e;
     if (f64) {
-        k_turb_spectrum<double><<<blocks, 256, 0, g->stream>>>((const double2*)src, (double2*)spec, n, tau, r2);
+        k_turb_spectrum<double><<<blocks, 256, 0, g->stream>>>((const double2*)src, (double2*)spec, n, tau, m2max);
         e = g->k64->dft2((double2*)spec, twiddles_fixed<double>(g->ws + g->lay.tw), true, g->stream);
         if (e == cudaSuccess) {
             k_turb_apply<double><<<blocks, 256, 0, g->stream>>>((double2*)field, (const double2*)spec, c, nn);
@@ -910,10 +926,10 @@ nlse_status nlse_turbulent_screen(nlse_grid* g, const void* xi, int xi_on_device
                                     g->stream);
         }
     } else {
-        k_turb_spectrum<float><<<blocks, 256, 0, g->stream>>>((const float2*)src, (float2*)spec, n, tau, r2);
+        k_turb_spectrum<float><<<blocks, 256, 0, g->stream>>>((const float2*)src, (float2*)spec, n, (float)tau, m2max);
         e = g->k32->dft2((float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw), true, g->stream);
         if (e == cudaSuccess) {
-            k_turb_apply<float><<<blocks, 256, 0, g->stream>>>((float2*)field, (const float2*)spec, c, nn);
+            k_turb_apply<float><<<blocks, 256, 0, g->stream>>>((float2*)field, (const float2*)spec, (float)c, nn);
             e = g->k32->row_forward((const float2*)field, (float2*)spec, twiddles_fixed<float>(g->ws + g->lay.tw),
                                     g->stream);
         }
@@ -948,6 +964,44 @@ nlse_status nlse_effective_lens(nlse_grid* g, const nlse_lens* lens, void* scrat
     if (g->p.precision == NLSE_FP64)
         return lens_impl<double>(g, lens, sc, count, centres, capacity, static_cast<double*>(w_dif_out));
     return lens_impl<float>(g, lens, sc, count, centres, capacity, static_cast<float*>(w_dif_out));
+}
+
+nlse_status nlse_moments(nlse_grid* g, int32_t count, const int32_t* p, const int32_t* q, double* out) {
+    if (!g || !p || !q || !out || count < 1 || count > kMomMax) return NLSE_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (p[k] < 1 || p[k] > 16 || q[k] < 0 || q[k] > 16) return NLSE_EINVAL;
+    if (!g->loaded) return NLSE_ESTATE;
+    // the per-block partials use the diagnostic slots: finalise pending records first
+    if (flush_diag_any(g) != NLSE_OK) return NLSE_ECUDA;
+    const int n = g->p.n;
+    const size_t nn = (size_t)n * n;
+    const bool f64 = g->p.precision == NLSE_FP64;
+    unsigned char* flu = g->ws + g->lay.aux;
+    nlse_status st = readout_any(g, nullptr, flu);
+    if (st != NLSE_OK) return st;
+    MomentSpec ms;
+    ms.count = count;
+    for (int k = 0; k < kMomMax; ++k) {
+        ms.p[k] = k < count ? p[k] : 1;
+        ms.q[k] = k < count ? q[k] : 0;
+    }
+    const int blocks = (int)std::min<size_t>((nn + 255) / 256, 152 * 4);
+    double* part = dat(g, g->lay.diag);
+    const double dx = g->p.L / n;
+    if (f64) k_moments<double><<<blocks, 256, 0, g->stream>>>((const double*)flu, n, dx, ms, part);
+    else k_moments<float><<<blocks, 256, 0, g->stream>>>((const float*)flu, n, dx, ms, part);
+    if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
+    std::vector<double> h((size_t)blocks * kMomMax);
+    if (cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+        return NLSE_ECUDA;
+    for (int k = 0; k < count; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += h[(size_t)b * kMomMax + k];
+        out[k] = s * dx * dx;
+    }
+    return NLSE_OK;
 }
 
 nlse_status nlse_history(nlse_grid* g, double* power, double* peak, int32_t capacity, int32_t* count) {

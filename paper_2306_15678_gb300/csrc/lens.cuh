@@ -39,17 +39,16 @@ __global__ void k_lens_fluence(const typename vec2<T>::type* __restrict__ field,
     }
 }
 
-// spectrum bin (q, p) *= exp(-l_dif (kx^2 + ky^2)) / n^2 (the 1/n^2 of the
-// inverse transform folded in); k_m = 2 pi m~ / L
+// spectrum bin (q, p) *= fx[p] fy[q], the separable factors of the low-pass
+// exp(-l_dif (kx^2 + ky^2)) = exp(-l_dif kx^2) exp(-l_dif ky^2), with the 1/n^2
+// of the inverse transform folded into fy (tables built on the host in FP64)
 template <typename T>
-__global__ void k_lens_filter(typename vec2<T>::type* wbuf, int n, double kunit, double l_dif) {
+__global__ void k_lens_filter(typename vec2<T>::type* wbuf, int n, const T* __restrict__ fx,
+                              const T* __restrict__ fy) {
     using V = typename vec2<T>::type;
     const size_t nn = (size_t)n * n;
-    const double inv_nn = 1.0 / (double)nn;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
-        const int q = (int)(i / n), p = (int)(i % n);
-        const double ky = kunit * (q < n / 2 ? q : q - n), kx = kunit * (p < n / 2 ? p : p - n);
-        const T f = (T)(exp(-l_dif * (kx * kx + ky * ky)) * inv_nn);
+        const T f = fx[i % n] * fy[i / n];
         const V v = wbuf[i];
         wbuf[i] = mk<V>(v.x * f, v.y * f);
     }

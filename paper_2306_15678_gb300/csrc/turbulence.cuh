@@ -8,19 +8,19 @@
 namespace nlse {
 
 // Spectral amplitude of the turbulent screen: out = tau xi on the bins with
-// p~^2 + q~^2 <= r2 (r2 = (k_h L / 2 pi)^2, signed bin numbers), 0 elsewhere;
-// row-major, rows = k_y.  out may alias xi.
+// p~^2 + q~^2 <= m2max (signed bin numbers; m2max = floor((k_h L / 2 pi)^2),
+// the same set as comparing the integer p~^2 + q~^2 with the real bound), 0
+// elsewhere; row-major, rows = k_y.  out may alias xi.
 template <typename T>
-__global__ void k_turb_spectrum(const typename vec2<T>::type* xi, typename vec2<T>::type* out, int n, double tau,
-                                double r2) {
+__global__ void k_turb_spectrum(const typename vec2<T>::type* xi, typename vec2<T>::type* out, int n, T tau,
+                                long long m2max) {
+    using V = typename vec2<T>::type;
     const size_t nn = (size_t)n * n;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
         const int q = (int)(i / n), p = (int)(i % n);
-        const int qq = q < n / 2 ? q : q - n, pp = p < n / 2 ? p : p - n;
-        const double m2 = (double)pp * pp + (double)qq * qq;
-        const typename vec2<T>::type v = xi[i];
-        out[i] = m2 <= r2 ? mk<typename vec2<T>::type>((T)(tau * (double)v.x), (T)(tau * (double)v.y))
-                          : mk<typename vec2<T>::type>((T)0, (T)0);
+        const long long qq = q < n / 2 ? q : q - n, pp = p < n / 2 ? p : p - n;
+        const V v = xi[i];
+        out[i] = pp * pp + qq * qq <= m2max ? mk<V>(tau * v.x, tau * v.y) : mk<V>((T)0, (T)0);
     }
 }
 
@@ -48,17 +48,20 @@ k_dft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __rest
     for (int m = 0; m < E; ++m) data[base + (size_t)(j + m * TL) * stride] = v[m];
 }
 
-// The turbulent layer on the row-major field: U <- U exp(-i c Re(eps)), the
-// phase taken in FP64 (c = thickness / (2 k0)).
+// The turbulent layer on the row-major field: U <- U exp(-i c Re(eps)),
+// c = thickness / (2 k0); the phase and its sine and cosine in the grid
+// precision.
+__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+
 template <typename T>
-__global__ void k_turb_apply(typename vec2<T>::type* field, const typename vec2<T>::type* __restrict__ eps,
-                             double c, size_t nn) {
+__global__ void k_turb_apply(typename vec2<T>::type* field, const typename vec2<T>::type* __restrict__ eps, T c,
+                             size_t nn) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
-        double sn, cs;
-        sincos(-c * (double)eps[i].x, &sn, &cs);
+        T sn, cs;
+        sincos_(-c * eps[i].x, &sn, &cs);
         const typename vec2<T>::type u = field[i];
-        field[i] = mk<typename vec2<T>::type>((T)((double)u.x * cs - (double)u.y * sn),
-                                              (T)((double)u.x * sn + (double)u.y * cs));
+        field[i] = mk<typename vec2<T>::type>(u.x * cs - u.y * sn, u.x * sn + u.y * cs);
     }
 }
 

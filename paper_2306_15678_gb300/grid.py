@@ -150,6 +150,10 @@ class Grid:
                                      cent.ctypes.data, cap, wd.data_ptr() if wd is not None else 0)
         return k, cent[:k].copy(), wd
 
+    def moments(self, pq):
+        """Eq. 8 moments M(p, q) = int I^p (x^2 + y^2)^q dx dy for the (p, q) pairs."""
+        return np.array(capi.nlse_moments(self.h, list(pq)))
+
     def history(self):
         cap = 4096
         pw = np.empty(cap)
