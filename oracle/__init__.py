@@ -180,6 +180,10 @@ def params(cfg: dict) -> OrcParams:
     th = cfg.get("theta", (1.0, 0.0, 1.0, 0.0, 1.0, 0.0))
     for i in range(6):
         p.theta[i] = float(th[i])
+    screen = cfg.get("screen", "frozen")
+    if screen not in ("frozen", "exact"):
+        raise ValueError(f"screen {screen!r}")
+    p.reserved = 1 if screen == "exact" else 0
     return p
 
 

@@ -67,7 +67,7 @@ typedef struct {
     int32_t n;        /* grid points per side, power of two */
     int32_t K;        /* multiphoton order m of Eq. 3 */
     uint32_t terms;   /* bit 0 Kerr, bit 1 plasma, bit 2 absorption, bit 3 diffraction */
-    int32_t reserved;
+    int32_t reserved; /* screen: 0 frozen at the entering intensity (Eq. 2), 1 exact substep */
     double L;         /* transverse window, cm */
     double dz;        /* z step, cm */
     double lambda0;   /* carrier wavelength, cm */
@@ -265,10 +265,51 @@ static void screen_exponent_dtheta(const screen_coef *c, const orc_params *p, do
     }
 }
 
-/* nonlinear half of the step: U <- v * exp(s(|v|^2)), screen held at |v|^2 */
+/* Exact pointwise substep (p->reserved == 1): the nonlinear part of Eq. 1-3
+ * over dz solved exactly instead of frozen at the entering intensity, for
+ * real gains (theta[1] = theta[3] = theta[5] = 0, K >= 2).  Pointwise the
+ * equation is dU/dz = -(i/(2 k0)) (c_K eps_k I + c_P eps_m I^K) U
+ * - (c_A beta_K / 2) I^(K-1) U, so the intensity obeys dI/dz = -b I^K
+ * (b = c_A beta_K) and the phase integrates the intensity:
+ *   I(z) = I0 (1 + a z/dz)^(-1/(K-1)),  a = (K-1) b I0^(K-1) dz,
+ *   int_0^dz I   = I0 dz [(1+a)^((K-2)/(K-1)) - 1] / (a (K-2)/(K-1))   (K = 2: ln(1+a)/a),
+ *   int_0^dz I^K = I0^K dz (K-1) [1 - (1+a)^(-1/(K-1))] / a,
+ * each factor 1 when a = 0; written with log1p / expm1 so small a loses nothing. */
+static void screen_exact_point(const orc_params *p, const screen_coef *c, cplx *u) {
+    cplx v = *u;
+    double I0 = creal(v) * creal(v) + cimag(v) * cimag(v);
+    int K = p->K;
+    double b = c->useA ? creal(c->cA) * p->betaK : 0.0;
+    double a = (double)(K - 1) * b * pow(I0, (double)(K - 1)) * p->dz;
+    double amp = 1.0, f1 = 1.0, fk = 1.0;
+    if (a != 0.0) {
+        double l = log1p(a);
+        amp = exp(-l / (2.0 * (K - 1)));
+        if (K == 2) f1 = l / a;
+        else {
+            double e = (double)(K - 2) / (double)(K - 1);
+            f1 = expm1(e * l) / (a * e);
+        }
+        fk = -(double)(K - 1) * expm1(-l / (double)(K - 1)) / a;
+    }
+    double bracket = 0.0;
+    if (c->useK) bracket += creal(c->cK) * c->eps_k * I0 * f1;
+    if (c->useP) bracket += creal(c->cP) * c->eps_m * pow(I0, (double)K) * fk;
+    double phase = -p->dz / (2.0 * c->k0) * bracket;
+    *u = v * amp * cexp(I * phase);
+}
+
+/* nonlinear half of the step: U <- v * exp(s(|v|^2)), screen held at |v|^2
+ * (or the exact substep above when p->reserved == 1) */
 void orc_screen(const orc_params *p, cplx *U) {
     if (!(p->terms & (ORC_KERR | ORC_PLASMA | ORC_MPA))) return;
     screen_coef c = make_coef(p);
+    if (p->reserved == 1) {
+        size_t nn0 = (size_t)p->n * p->n;
+#pragma omp parallel for schedule(static)
+        for (size_t i = 0; i < nn0; ++i) screen_exact_point(p, &c, &U[i]);
+        return;
+    }
     size_t nn = (size_t)p->n * p->n;
 #pragma omp parallel for schedule(static)
     for (size_t i = 0; i < nn; ++i) {

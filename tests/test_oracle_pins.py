@@ -538,6 +538,73 @@ def test_turbulent_layer_acts_like_the_kerr_term():
     assert rel_max(U, oracle.screen(v, cfg)) < 1e-10
 
 
+# ------------------------------------- exact pointwise substep (Eqs. 1-3)
+
+def rk4_point(u, cfg, dz, nsub=4000):
+    """The pointwise nonlinear equation of Eqs. 1-3 integrated by RK4 with
+    nsub substeps: dU/dz = [-(i/2k0)(c_K eps_k I + c_P eps_m I^K)
+    - (c_A beta_K / 2) I^(K-1)] U (real gains)."""
+    k0 = 2 * math.pi * cfg["n0"] / cfg["lambda0"]
+    eps_k = 2 * k0 * k0 * cfg["n2"] / cfg["n0"]
+    eps_m = -k0 * k0 * cfg["sigmaK"] * cfg["rho_nt"] * cfg["tau_pl"] / cfg["rho_c"]
+    th, K, t = cfg["theta"], cfg["K"], cfg["terms"]
+
+    def f(U):
+        I = np.abs(U) ** 2
+        br = (th[0] * eps_k * I if t & configs.KERR else 0) + (th[2] * eps_m * I ** K if t & configs.PLASMA else 0)
+        damp = (th[4] * cfg["betaK"] / 2 * I ** (K - 1)) if t & configs.MPA else 0
+        return (-1j / (2 * k0) * br - damp) * U
+
+    h = dz / nsub
+    for _ in range(nsub):
+        k1 = f(u)
+        k2 = f(u + h / 2 * k1)
+        k3 = f(u + h / 2 * k2)
+        k4 = f(u + h * k3)
+        u = u + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return u
+
+
+@pytest.mark.parametrize("K", [2, 3, 8])
+def test_exact_substep_matches_rk4(K):
+    """The exact substep against an RK4 solution of the same pointwise
+    equation (all three terms, gains 0.9 / 0.05 / 1.5, intensities from weak to
+    strongly absorbing)."""
+    cfg = dict(configs.physics(4, 1.0, 0.8, configs.KERR | configs.PLASMA | configs.MPA,
+                               theta=(0.9, 0.0, 0.05, 0.0, 1.5, 0.0)), K=K, screen="exact")
+    if K != 8:  # keep absorption and plasma O(1) over the step for the other orders
+        cfg["betaK"] = 0.3 / (3e13 ** (K - 1))
+        cfg["sigmaK"] = cfg["sigmaK"] * 3e13 ** (8 - K)
+    I = np.array([1e11, 2e13, 5e13, 7e13])
+    v = (np.sqrt(I) * np.exp(1j * np.array([0.1, 1.0, 2.0, -2.5]))).astype(complex)
+    out = oracle.screen(np.tile(v, (4, 1)), cfg)[0]
+    ref = rk4_point(v.copy(), cfg, cfg["dz"])
+    assert np.max(np.abs(out - ref) / np.abs(v)) < 1e-10
+    assert np.max(np.abs(out) / np.abs(v)) <= 1.0 and np.min(np.abs(out) / np.abs(v)) < 0.95
+
+
+def test_exact_substep_without_absorption_is_the_frozen_screen():
+    """With no absorption the intensity is constant over the step, so the
+    exact substep and the frozen screen of Eq. 2 agree exactly (up to rounding)."""
+    cfg = configs.physics(16, 1.0, 0.5, configs.KERR | configs.PLASMA, theta=(0.9, 0.0, 1.1, 0.0, 1.0, 0.0))
+    v = field_with_intensity(16, 4e13, np.random.default_rng(7))
+    a = oracle.screen(v, cfg)
+    b = oracle.screen(v, dict(cfg, screen="exact"))
+    assert rel_max(b, a) < 1e-13
+
+
+def test_exact_and_frozen_screens_differ_at_second_order():
+    """Both are consistent with the pointwise equation: their one-step
+    difference falls by 4 when dz halves."""
+    base = configs.physics(8, 1.0, 0.4, configs.ALL_TERMS)
+    v = field_with_intensity(8, 5e13, np.random.default_rng(8))
+    d = []
+    for dz in (0.4, 0.2, 0.1):
+        c = dict(base, dz=dz)
+        d.append(np.max(np.abs(oracle.screen(v, dict(c, screen="exact")) - oracle.screen(v, c))))
+    assert 3.6 < d[0] / d[1] < 4.4 and 3.6 < d[1] / d[2] < 4.4
+
+
 # ------------------------------------------------ moments (Eq. 8)
 
 def test_moments_gaussian_closed_form():
@@ -692,6 +759,10 @@ MUTANTS = [
      "S[(size_t)q * n + c] = (m2 > r2) ?", "turb_line"),
     ("turbulent screen without the n^2 of the unnormalised sum", "eps[i] = creal(S[i]) * (double)nn;",
      "eps[i] = creal(S[i]);", "turb_line"),
+    ("exact substep amplitude without the square root", "amp = exp(-l / (2.0 * (K - 1)));",
+     "amp = exp(-l / (double)(K - 1));", "exact"),
+    ("exact substep Kerr integral with the wrong exponent", "double e = (double)(K - 2) / (double)(K - 1);",
+     "double e = (double)(K - 1) / (double)(K - 2);", "exact"),
     ("moment about the window corner", "double xc = ((double)x - n / 2 + 0.5) * dx;",
      "double xc = ((double)x) * dx;", "moments"),
     ("moment radius exponent q instead of 2q", "pow(xc * xc + yc * yc, (double)q)",
@@ -734,6 +805,7 @@ def test_planted_mistake_is_caught(name, orig, repl, pin, tmp_path, monkeypatch)
         "lens_value": test_lens_value_is_piecewise_eq6,
         "lens_apply": test_lens_apply_closed_form_and_superposition,
         "moments": test_moments_gaussian_closed_form,
+        "exact": lambda: test_exact_substep_matches_rk4(8),
     }
     with pytest.raises(AssertionError):
         pins[pin]()
