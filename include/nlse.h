@@ -96,14 +96,20 @@ typedef struct nlse_params {
     double betaK;         /* K-photon absorption coefficient, cm^(2K-3) W^(1-K) */
     double theta[6];      /* complex screen gains (re, im) for Kerr, plasma, absorption */
     int32_t diag_every;   /* record power and peak every this many steps (0 = never) */
-    int32_t scheme;       /* NLSE_LIE or NLSE_STRANG (see nlse_step) */
+    int32_t scheme;       /* NLSE_LIE or NLSE_STRANG, optionally | NLSE_EXACT_SCREEN */
 } nlse_params;
 
 /* Splitting of a step (Eq. 2): NLSE_LIE -- diffraction over dz, then the screen
  * over dz; NLSE_STRANG -- the screen over dz/2, diffraction over dz, the screen
- * over dz/2 (symmetric, second order in dz).  The batched march and the
- * adjoint take NLSE_LIE only. */
-enum { NLSE_LIE = 0, NLSE_STRANG = 1 };
+ * over dz/2 (symmetric, second order in dz).  OR NLSE_EXACT_SCREEN in to
+ * replace the screen frozen at the entering intensity by the exact pointwise
+ * substep of the nonlinear part of Eqs. 1-3: for real gains (theta[1] =
+ * theta[3] = theta[5] = 0) and K >= 2 the intensity obeys dI/dz = -c_A beta_K
+ * I^K, so I(z) = I0 (1 + (K-1) c_A beta_K I0^(K-1) z)^(-1/(K-1)), and the Kerr
+ * and plasma phases are the closed-form integrals of I and I^K over the step
+ * (NLSE_EINVAL for complex gains or K < 2).  The batched march and the adjoint
+ * take NLSE_LIE only (NLSE_EUNSUPPORTED otherwise). */
+enum { NLSE_LIE = 0, NLSE_STRANG = 1, NLSE_EXACT_SCREEN = 2 };
 
 typedef struct nlse_grid nlse_grid;
 

@@ -16,6 +16,7 @@ NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
 NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
 NLSE_COL_TMA = 0x100  # column tile staged with bulk tensor copies (or'ed with the width)
 NLSE_LIE, NLSE_STRANG = 0, 1  # splitting of a step
+NLSE_EXACT_SCREEN = 2  # or'ed into the scheme: exact pointwise substep instead of the frozen screen
 NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15
 NLSE_FP64, NLSE_FP32 = 0, 1
 

@@ -85,7 +85,10 @@ nlse_status validate(const nlse_params* p) {
     if ((p->terms & NLSE_PLASMA) && !(p->rho_c > 0.0)) return NLSE_EINVAL;
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(p->theta[i])) return NLSE_EINVAL;
-    if (p->diag_every < 0 || (p->scheme != NLSE_LIE && p->scheme != NLSE_STRANG)) return NLSE_EINVAL;
+    if (p->diag_every < 0 || p->scheme < 0 || p->scheme > (NLSE_STRANG | NLSE_EXACT_SCREEN)) return NLSE_EINVAL;
+    // the exact substep has a closed form for real gains and K >= 2 only
+    if ((p->scheme & NLSE_EXACT_SCREEN) && (p->theta[1] != 0.0 || p->theta[3] != 0.0 || p->theta[5] != 0.0 || p->K < 2))
+        return NLSE_EINVAL;
     return NLSE_OK;
 }
 
@@ -174,6 +177,8 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     c.has_gain = (c.re_k != (T)0 || c.re_p != (T)0 || c.re_a != (T)0) ? 1 : 0;
     c.reps = 1;
     c.scale = (T)1;
+    c.exact = (p->scheme & NLSE_EXACT_SCREEN) ? 1 : 0;
+    c.ka = (T)(-2.0 * (p->K - 1) * th[4] * aA);  // (K-1) c_A beta_K dz I_ref^(K-1)
     return c;
 }
 
@@ -363,7 +368,7 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
     VT<T>* field = at<T>(g, g->lay.state);
     const int n = g->p.n;
     double* partials = dat(g, g->lay.partials);
-    const bool strang = g->p.scheme == NLSE_STRANG;
+    const bool strang = (g->p.scheme & NLSE_STRANG) != 0;
     ScreenCoef<T> sc = Sel<T>::sc(g);
     for (int s = 0; s < nsteps; ++s) {
         if (ev && cudaEventRecord(ev[2 * s], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -673,7 +678,7 @@ nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_works
     const int k = log2_exact(p->n);
     if (cudaGetDevice(&g->device) != cudaSuccess) { delete g; return NLSE_ECUDA; }
     nlse_params screen_p = *p;  // the screen of one Lie step, or half of a symmetric step
-    if (p->scheme == NLSE_STRANG) screen_p.dz = 0.5 * p->dz;
+    if (p->scheme & NLSE_STRANG) screen_p.dz = 0.5 * p->dz;
     if (p->precision == NLSE_FP64) {
         g->k64 = kernels_f64(k);
         g->cols = g->k64->col_default;

@@ -31,6 +31,9 @@ template <typename T> struct ScreenCoef {
     T scale;       // factor on the field entering the screen: 1, or 1/n for a
                    // row pass not preceded by a column pass (whose tables carry
                    // the 1/n^2 of the inverse transforms); a power of two, exact
+    int exact;     // 1: the exact pointwise substep (real gains) instead of the
+                   // frozen screen; its absorption number is a = ka u^(K-1)
+    T ka;          // (K-1) c_A beta_K dz I_ref^(K-1)
 };
 
 template <typename T> __device__ __forceinline__ T ipow(T u, int e) {
@@ -163,6 +166,43 @@ __device__ __forceinline__ double2 apply_screen(double2 v, const ScreenCoef<doub
     sincos(im, &sn, &cs);
     const double pr = amp * cs, pi = amp * sn;
     return mk<double2>(v.x * pr - v.y * pi, v.x * pi + v.y * pr);
+}
+
+// sine and cosine in the precision of the argument
+__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+
+// Exact pointwise substep (real gains, K >= 2): over the step the intensity
+// follows dI/dz = -b I^K, I(dz) = I0 (1 + a)^(-1/(K-1)) with a = ka u^(K-1),
+// and the phase is the screen's Kerr and plasma coefficients times the step
+// averages of u and u^K:
+//   <u>   = u   [(1+a)^((K-2)/(K-1)) - 1] / (a (K-2)/(K-1))   (K = 2: ln(1+a)/a),
+//   <u^K> = u^K (K-1) [1 - (1+a)^(-1/(K-1))] / a,
+// both 1 at a = 0; log1p and expm1 keep small a exact.  Kept out of line: the
+// frozen screen's register allocation in the row pass stays as it is.
+template <typename T>
+__device__ __noinline__ typename vec2<T>::type apply_screen_exact(typename vec2<T>::type v, T inv_iref, T im_k,
+                                                                  T im_p, T ka, int K) {
+    const T u = (v.x * v.x + v.y * v.y) * inv_iref;
+    const T uk1 = ipow(u, K - 1), uk = uk1 * u;
+    const T a = ka * uk1;
+    T amp = (T)1, f1 = (T)1, fk = (T)1;
+    if (a != (T)0) {
+        const T l = log1p(a), km1 = (T)(K - 1);
+        amp = exp(-l / ((T)2 * km1));
+        if (K == 2) {
+            f1 = l / a;
+        } else {
+            const T e = (T)(K - 2) / km1;
+            f1 = expm1(e * l) / (a * e);
+        }
+        fk = -km1 * expm1(-l / km1) / a;
+    }
+    const T ph = im_k * u * f1 + im_p * uk * fk;
+    T sn, cs;
+    sincos_(ph, &sn, &cs);
+    const T pr = amp * cs, pi = amp * sn;
+    return mk<typename vec2<T>::type>(v.x * pr - v.y * pi, v.x * pi + v.y * pr);
 }
 
 // ------------------------------------------------------------- reductions --
@@ -411,8 +451,14 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
 #pragma unroll 1
             for (int rep = 0; rep < sc.reps; ++rep) {
                 if (sc.active) {
+                    if (sc.exact) {  // (uniform)
 #pragma unroll
-                    for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc, warp);
+                        for (int m = 0; m < E; ++m)
+                            v[m] = apply_screen_exact<T>(v[m], sc.inv_iref, sc.im_k, sc.im_p, sc.ka, sc.K);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < E; ++m) v[m] = apply_screen(v[m], sc, warp);
+                    }
                 }
                 if (DIAG && rep == 0) {
 #pragma unroll

@@ -50,10 +50,7 @@ k_dft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __rest
 
 // The turbulent layer on the row-major field: U <- U exp(-i c Re(eps)),
 // c = thickness / (2 k0); the phase and its sine and cosine in the grid
-// precision.
-__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
-
+// precision (sincos_ in kernels.cuh).
 template <typename T>
 __global__ void k_turb_apply(typename vec2<T>::type* field, const typename vec2<T>::type* __restrict__ eps, T c,
                              size_t nn) {

@@ -30,7 +30,10 @@ def make_params(cfg: dict, precision: str | None = None, diag_every: int = 0) ->
     scheme = cfg.get("scheme", "lie")
     if scheme not in _SCHEME:
         raise ValueError(f"scheme {scheme!r}: expected 'lie' or 'strang'")
-    p.scheme = _SCHEME[scheme]
+    screen = cfg.get("screen", "frozen")
+    if screen not in ("frozen", "exact"):
+        raise ValueError(f"screen {screen!r}: expected 'frozen' or 'exact'")
+    p.scheme = _SCHEME[scheme] | (capi.NLSE_EXACT_SCREEN if screen == "exact" else 0)
     return p
 
 

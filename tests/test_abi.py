@@ -46,7 +46,7 @@ def test_workspace_size_and_validation_on_host():
            ("n", 4, capi.NLSE_EUNSUPPORTED), ("precision", 7, capi.NLSE_EUNSUPPORTED),
            ("K", 0, capi.NLSE_EINVAL), ("terms", 16, capi.NLSE_EINVAL),
            ("L", -1.0, capi.NLSE_EINVAL), ("dz", 0.0, capi.NLSE_EINVAL),
-           ("diag_every", -1, capi.NLSE_EINVAL), ("scheme", 2, capi.NLSE_EINVAL)]
+           ("diag_every", -1, capi.NLSE_EINVAL), ("scheme", 4, capi.NLSE_EINVAL)]
     for field, val, code in bad:
         q = make_params(cfg)
         setattr(q, field, val)
@@ -123,3 +123,34 @@ def test_lens_scratch_size_and_null_checks():
     assert ei.value.status == capi.NLSE_EINVAL
     with pytest.raises(ValueError):
         capi.make_lens(dict(l_dif=0.0, w_l=1.0, re=[(0.1 * (j + 1), 1, 1, 0) for j in range(9)]))
+
+
+def test_exact_screen_validation_on_host():
+    """The exact substep takes real gains and K >= 2; the batched march and the
+    adjoint take the plain Lie step only."""
+    cfg = dict(configs.cfg_plain_fp64(), screen="exact")
+    p = make_params(cfg)
+    assert p.scheme == capi.NLSE_EXACT_SCREEN
+    assert capi.nlse_workspace_size(p) > 0
+    p.scheme = capi.NLSE_STRANG | capi.NLSE_EXACT_SCREEN
+    assert capi.nlse_workspace_size(p) > 0
+    for field, val in (("theta", (1.0, 0.1, 1.0, 0.0, 1.0, 0.0)), ("K", 1)):
+        q = make_params(cfg)
+        if field == "theta":
+            for i, t in enumerate(val):
+                q.theta[i] = t
+        else:
+            q.K = val
+        with pytest.raises(capi.NlseError) as ei:
+            capi.nlse_workspace_size(q)
+        assert ei.value.status == capi.NLSE_EINVAL
+    q = make_params(cfg)
+    q.scheme = 4
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_workspace_size(q)
+    assert ei.value.status == capi.NLSE_EINVAL
+    with pytest.raises(capi.NlseError) as ei:
+        capi.nlse_adjoint_workspace_size(make_params(cfg), 10, 2)
+    assert ei.value.status == capi.NLSE_EUNSUPPORTED
+    with pytest.raises(ValueError):
+        make_params(dict(cfg, screen="implicit"))
