@@ -5,8 +5,9 @@
 //
 // Labelling in four launches over a row-major int32 label array:
 //  1. runs:   one block per row labels each pixel with w >= w_p by the index
-//             of the first pixel of its horizontal run (a block max-scan of
-//             run starts), every other pixel by -1;
+//             of the first pixel of its horizontal run (block max-scans of
+//             run starts over coalesced chunks of the row), every other pixel
+//             by -1;
 //  2. merge:  the runs of neighbouring rows that touch are joined by a
 //             concurrent union-find over the run starts: the larger of two
 //             roots is linked under the smaller with atomicMin, and a union
@@ -27,48 +28,40 @@ namespace nlse {
 constexpr int kHotUnionTries = 1 << 20;  // bound on the retries of one union (never reached)
 constexpr int kHotStatusGaveUp = 1;      // bit of the per-call status word
 
-// 1. runs: blockDim = min(n, 256) threads, each over n / blockDim contiguous
-// pixels; pixel (y, x) of the row-major input is w[(y n + x) stride] (stride 2
-// reads the real parts of a complex array)
+// 1. runs: one block of blockDim = min(n, 256) threads per row, sweeping the
+// row in chunks of blockDim consecutive pixels (coalesced); pixel (y, x) of the
+// row-major input is w[(y n + x) stride] (stride 2 reads the real parts of a
+// complex array).  A pixel starts a run when it is on and its left neighbour is
+// not; its label is the last run start at or before it: a block max-scan of
+// the starts within the chunk, carried over from the previous chunks.
 template <typename T>
 __global__ void __launch_bounds__(256) k_hot_runs(const T* __restrict__ w, int n, int stride, T wp,
                                                   int* __restrict__ label) {
     __shared__ int warp_last[8];
+    __shared__ int carry_s;
     const int y = blockIdx.x;
-    const int E = n / blockDim.x;
     const T* row = w + (size_t)y * n * stride;
     int* lrow = label + (size_t)y * n;
-    const int x0 = threadIdx.x * E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
-
-    // the last run start inside this thread's pixels
-    const bool left_on = x0 > 0 && row[(size_t)(x0 - 1) * stride] >= wp;
-    int last = -1;
-    bool prev = left_on;
-    for (int k = 0; k < E; ++k) {
-        const bool on = row[(size_t)(x0 + k) * stride] >= wp;
-        if (on && !prev) last = x0 + k;
-        prev = on;
-    }
-    // the last run start before this thread's pixels: exclusive max-scan
-    int incl = last;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(mask, incl, o);
-        if (lane >= o) incl = max(incl, v);
-    }
-    if (lane == 31 || threadIdx.x == blockDim.x - 1) warp_last[warp] = incl;
-    __syncthreads();
-    int cur = __shfl_up_sync(mask, incl, 1);
-    if (lane == 0) cur = -1;
-    for (int k = 0; k < warp; ++k) cur = max(cur, warp_last[k]);
-
-    prev = left_on;
-    for (int k = 0; k < E; ++k) {
-        const bool on = row[(size_t)(x0 + k) * stride] >= wp;
-        if (on && !prev) cur = x0 + k;
-        lrow[x0 + k] = on ? y * n + cur : -1;
-        prev = on;
+    int carry = -1;  // last run start before the chunk
+    for (int x0 = 0; x0 < n; x0 += blockDim.x) {
+        const int x = x0 + threadIdx.x;
+        const bool on = row[(size_t)x * stride] >= wp;
+        const bool left_on = x > 0 && row[(size_t)(x - 1) * stride] >= wp;
+        int incl = on && !left_on ? x : -1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(mask, incl, o);
+            if (lane >= o) incl = max(incl, v);
+        }
+        if (lane == 31 || threadIdx.x == blockDim.x - 1) warp_last[warp] = incl;
+        __syncthreads();
+        int cur = max(carry, incl);
+        for (int k = 0; k < warp; ++k) cur = max(cur, warp_last[k]);
+        lrow[x] = on ? y * n + cur : -1;
+        if (threadIdx.x == blockDim.x - 1) carry_s = cur;
+        __syncthreads();
+        carry = carry_s;
     }
 }
 

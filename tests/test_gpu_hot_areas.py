@@ -126,3 +126,17 @@ def test_filamented_beam():
         for frac in (0.1, 0.3):
             count, _ = check_against_oracle(g, frac * peak, 4, "fp32")
             assert count >= 1
+
+
+def test_maximum_size_8192():
+    """The largest grid (8192^2 FP32): 4-neighbour labels identical to the
+    oracle's on a mask at the percolation threshold (one spanning region
+    of ~10^7 pixels and ~10^6 small ones)."""
+    n = 8192
+    U0 = noise_field(n, 77).astype(np.complex64)
+    with Grid(grid_cfg(n), precision="fp32") as g:
+        g.load(U0)
+        F = g.fluence()
+        wp = float(np.quantile(F[::4, ::4].astype(np.float64), 1.0 - 0.593))
+        count, _ = check_against_oracle(g, wp, 4, "fp32")
+        assert count > 10000
