@@ -185,16 +185,21 @@ cudaError_t launch_row_forward(const typename vec2<T>::type* src, typename vec2<
     return cudaGetLastError();
 }
 
+template <typename T, int N, bool COLS, bool INV>
+cudaError_t launch_dft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* tw, cudaStream_t s) {
+    constexpr int LPB = dft_lines_per_block<T, N, COLS>(), THREADS = threads_per_line<T, N>() * LPB;
+    constexpr int SMEM = line_stride<T, N, LPB>() * LPB * (int)sizeof(typename vec2<T>::type);
+    cudaError_t e = ensure_smem<k_dft_lines<T, N, COLS, INV>>(SMEM);
+    if (e != cudaSuccess) return e;
+    k_dft_lines<T, N, COLS, INV><<<N / LPB, THREADS, SMEM, s>>>(data, tw);
+    return cudaGetLastError();
+}
+
 template <typename T, int N, bool INV>
 cudaError_t launch_dft2_dir(typename vec2<T>::type* data, const typename tab_of<T>::type* tw, cudaStream_t s) {
-    constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
-    constexpr int SMEM = row_smem_bytes<T, N>();
-    cudaError_t e = ensure_smem<k_dft_lines<T, N, false, INV>>(SMEM);
-    if (e == cudaSuccess) e = ensure_smem<k_dft_lines<T, N, true, INV>>(SMEM);
+    cudaError_t e = launch_dft_lines<T, N, false, INV>(data, tw, s);
     if (e != cudaSuccess) return e;
-    k_dft_lines<T, N, false, INV><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
-    k_dft_lines<T, N, true, INV><<<N / RPB, THREADS, SMEM, s>>>(data, tw);
-    return cudaGetLastError();
+    return launch_dft_lines<T, N, true, INV>(data, tw, s);
 }
 
 template <typename T, int N>

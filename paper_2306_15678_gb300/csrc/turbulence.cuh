@@ -24,21 +24,40 @@ __global__ void k_turb_spectrum(const typename vec2<T>::type* xi, typename vec2<
     }
 }
 
+// Lines per block of the column transform: adjacent columns are read together,
+// so that a warp's loads fill whole 32-byte sectors (4 complex64 or 2
+// complex128 columns), within 1024 threads per block; small grids keep the row
+// kernels' lines per block.
+template <typename T, int N> __host__ __device__ constexpr int dft_cols_per_block() {
+    constexpr int TL = threads_per_line<T, N>();
+    constexpr int sect = 32 / (2 * (int)sizeof(T));
+    constexpr int by_threads = 1024 / TL;
+    constexpr int l = sect < by_threads ? sect : by_threads;
+    constexpr int rpb = rows_per_block<T, N>();
+    return rpb > l ? rpb : l;
+}
+template <typename T, int N, bool COLS> __host__ __device__ constexpr int dft_lines_per_block() {
+    return COLS ? dft_cols_per_block<T, N>() : rows_per_block<T, N>();
+}
+
 // Unnormalised DFT (forward, or inverse when INV) of every line of a row-major
 // n x n array, in place: rows (along x) when COLS is false, columns (along y)
-// when true.  Every line is loaded before the first exchange barrier and
-// stored after the last, so the transform may overwrite its input.
+// when true.  Column blocks hold adjacent columns with the column index fastest
+// across the threads (coalesced sectors).  Every line is loaded before the
+// first exchange barrier and stored after the last, so the transform may
+// overwrite its input.
 template <typename T, int N, bool COLS, bool INV>
-__global__ void __launch_bounds__(threads_per_line<T, N>() * rows_per_block<T, N>(),
-                                  min_blocks<threads_per_line<T, N>() * rows_per_block<T, N>()>())
+__global__ void __launch_bounds__(threads_per_line<T, N>() * dft_lines_per_block<T, N, COLS>(),
+                                  min_blocks<threads_per_line<T, N>() * dft_lines_per_block<T, N, COLS>()>())
 k_dft_lines(typename vec2<T>::type* data, const typename tab_of<T>::type* __restrict__ tw) {
     using V = typename vec2<T>::type;
-    constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), RPB = rows_per_block<T, N>();
-    constexpr int LS = line_stride<T, N, RPB>();
+    constexpr int E = elems<T, N>(), TL = threads_per_line<T, N>(), LPB = dft_lines_per_block<T, N, COLS>();
+    constexpr int LS = line_stride<T, N, LPB>();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* smem = reinterpret_cast<V*>(smraw);
-    const int g = row_of_thread<TL, RPB>(), j = lane_in_row<TL, RPB>();
-    const size_t line = (size_t)blockIdx.x * RPB + g;
+    const int g = COLS ? (int)(threadIdx.x % LPB) : row_of_thread<TL, LPB>();
+    const int j = COLS ? (int)(threadIdx.x / LPB) : lane_in_row<TL, LPB>();
+    const size_t line = (size_t)blockIdx.x * LPB + g;
     const size_t base = COLS ? line : line * N, stride = COLS ? N : 1;
     V v[E];
 #pragma unroll
