@@ -140,8 +140,9 @@ def p_vector(moments_per_plane) -> np.ndarray:
     """[log Q^1, log P] for every (beam, plane) pair, in order."""
     v = []
     for q1, pw in moments_per_plane:
-        v += [math.log(q1), math.log(pw)]
-    return np.array(v)
+        v += [q1, pw]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.log(np.array(v, dtype=np.float64))  # non-finite for a march that blew up
 
 
 class BatchFitness:
@@ -159,6 +160,7 @@ class BatchFitness:
         self.P0 = self.vectors([target_gene])[0]
 
     def _grid(self, c):
+        # one helper grid per (n, L): it only holds a field for its moments
         key = (c["n"], c["L"])
         if key not in self._grids:
             self._grids[key] = Grid(dict(c, theta=(1, 0, 1, 0, 1, 0)), precision="fp32", device=self.device)
