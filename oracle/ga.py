@@ -118,6 +118,13 @@ def search(fitness, lo, hi, draws, elite=5, pop=10, probe=20, batch=10, max_batc
     return dict(gene=el[ib][0], fitness=el[ib][1], f_el=level, history=best_hist, elite=el, draws_used=pos[0])
 
 
+def _log(x):
+    """log, with -inf at 0 and nan for negative or nan input (a blown-up march)."""
+    if x > 0.0:
+        return math.log(x)
+    return -math.inf if x == 0.0 else math.nan
+
+
 def p_vectors(genes, cfgs, fields, steps, samples):
     """P of each gene: [log M(1,1), log M(1,0)] per (plane, beam) from the FP64 march."""
     k = steps // samples
@@ -136,7 +143,7 @@ def p_vectors(genes, cfgs, fields, steps, samples):
         for s in range(samples):
             for b in range(len(cfgs)):
                 q1, pw = per_beam[b][s]
-                v += [math.log(q1), math.log(pw)]
+                v += [_log(q1), _log(pw)]
         out.append(np.array(v))
     return out
 
