@@ -2,6 +2,7 @@
 // grid size n = 2^k (8..8192) and precision, gathered into per-size tables.
 #pragma once
 #include <cuda_runtime.h>
+#include <utility>
 
 #include <cudaTypedefs.h>
 
@@ -69,6 +70,22 @@ template <typename T, int N, int C> constexpr bool col_valid() {
     return C <= N && threads_per_line<T, N>() * C <= 1024 && col_smem_bytes<T, N, C>() <= kMaxSmem;
 }
 
+// Launch with programmatic stream serialisation (see pdl_trigger / pdl_wait).
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, int smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 template <typename T, int N>
 cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
                             const typename tab_of<T>::type* tw, ScreenCoef<T> sc, double* partials,
@@ -78,12 +95,12 @@ cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>:
     cudaError_t e;
     if (diag) {
         if ((e = ensure_smem<k_row_pass<T, N, true>>(SMEM)) != cudaSuccess) return e;
-        k_row_pass<T, N, true><<<N / RPB, THREADS, SMEM, s>>>(src, dst, tw, sc, partials);
+        e = launch_pdl(k_row_pass<T, N, true>, dim3(N / RPB), dim3(THREADS), SMEM, s, src, dst, tw, sc, partials);
     } else {
         if ((e = ensure_smem<k_row_pass<T, N, false>>(SMEM)) != cudaSuccess) return e;
-        k_row_pass<T, N, false><<<N / RPB, THREADS, SMEM, s>>>(src, dst, tw, sc, partials);
+        e = launch_pdl(k_row_pass<T, N, false>, dim3(N / RPB), dim3(THREADS), SMEM, s, src, dst, tw, sc, partials);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T, int N, int C>
@@ -145,9 +162,9 @@ cudaError_t launch_col_tma_c(const typename vec2<T>::type* src, typename vec2<T>
         }
         if (e == cudaSuccess) e = ensure_smem<k_col_pass_tma<T, N, C>>(SMEM);
         if (e != cudaSuccess) return e;
-        k_col_pass_tma<T, N, C><<<N / C, threads_per_line<T, N>() * C, SMEM, s>>>(ml, ms, tw, px, py, rot, status,
-                                                                                  extra_tx);
-        return cudaGetLastError();
+        e = launch_pdl(k_col_pass_tma<T, N, C>, dim3(N / C), dim3(threads_per_line<T, N>() * C), SMEM, s, ml, ms, tw,
+                       px, py, rot, status, extra_tx);
+        return e != cudaSuccess ? e : cudaGetLastError();
     } else {
         return cudaErrorInvalidConfiguration;
     }

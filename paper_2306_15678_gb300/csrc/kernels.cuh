@@ -511,6 +511,14 @@ __device__ __forceinline__ void col_tile(const typename vec2<T>::type* src, type
     for (int m = 0; m < E; ++m) M::st(dst + sidx<N>(j + m * TL, col), v[m]);
 }
 
+// Programmatic dependent launch between the passes of the march: a pass lets
+// the next pass's blocks be scheduled as soon as all of its own blocks are
+// running (their set-up then overlaps its last wave), and waits for the full
+// completion, with its memory, of the pass before it ahead of any access to the
+// field.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Row pass kernel of the march; with DIAG the block also reduces sum |U|^2 and
 // max |U|^2 of its rows into partials.
 template <typename T, int N, bool DIAG>
@@ -522,6 +530,8 @@ k_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
     constexpr int RPB = rows_per_block<T, N>();
     extern __shared__ __align__(16) unsigned char smraw[];
     T tsum = (T)0, tmax = (T)0;
+    pdl_trigger();
+    pdl_wait();
     row_tile<T, N, RPB, DIAG, MemPlain>(src, dst, tw, sc, blockIdx.x * RPB, reinterpret_cast<V*>(smraw),
                                         tsum, tmax);
     if constexpr (DIAG) block_partials<T>(tsum, tmax, partials);

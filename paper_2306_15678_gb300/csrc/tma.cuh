@@ -131,6 +131,8 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
     const int col0 = blockIdx.x * C;
     // stage index of (y, c): [y/2][c][y mod 2]
     auto st = [](int y, int c) { return C == 1 ? y : ((y >> 1) * C + c) * 2 + (y & 1); };
+    pdl_trigger();
+    pdl_wait();
     if (threadIdx.x == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
