@@ -410,11 +410,16 @@ template <int TL, int RPB> __device__ __forceinline__ int lane_in_row() {
 // Global-memory access policies of the tile bodies: plain accesses for the
 // per-pass kernels, L2-only (.cg) accesses for the persistent batched kernel,
 // whose tiles are rewritten by other SMs within the same launch.
+// kExactScreen: whether the body carries the exact pointwise substep (the
+// batched march takes the frozen screen only, and its persistent kernel keeps
+// the registers the substep's call would cost).
 struct MemPlain {
+    static constexpr bool kExactScreen = true;
     template <typename V> __device__ __forceinline__ static V ld(const V* p) { return *p; }
     template <typename V> __device__ __forceinline__ static void st(V* p, V v) { *p = v; }
 };
 struct MemCG {
+    static constexpr bool kExactScreen = false;
     template <typename V> __device__ __forceinline__ static V ld(const V* p) { return __ldcg(p); }
     template <typename V> __device__ __forceinline__ static void st(V* p, V v) { __stcg(p, v); }
 };
@@ -451,7 +456,7 @@ __device__ __forceinline__ void row_tile(const typename vec2<T>::type* src, type
 #pragma unroll 1
             for (int rep = 0; rep < sc.reps; ++rep) {
                 if (sc.active) {
-                    if (sc.exact) {  // (uniform)
+                    if (M::kExactScreen && sc.exact) {  // (uniform)
 #pragma unroll
                         for (int m = 0; m < E; ++m)
                             v[m] = apply_screen_exact<T>(v[m], sc.inv_iref, sc.im_k, sc.im_p, sc.ka, sc.K);
