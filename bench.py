@@ -452,8 +452,12 @@ def main():
                 h1.record(stream)
                 torch.cuda.synchronize(dev)
                 ts.append(h0.elapsed_time(h1))
+            # HBM sweeps of the implementation, bytes per point (FP32 grid): readout 12,
+            # runs 8, merge 4, roots 4, spread 8
+            hot_gbs = 36.0 * n * n / (min(ts) / 1e3) / 1e9
             hot = {"w_p_w_per_cm2": wp, "connectivity": 4, "count": count, "ms": min(ts),
-                   "steps_marched": g.steps_taken,
+                   "steps_marched": g.steps_taken, "sweep_bytes_per_point": 36, "sweep_gbs": hot_gbs,
+                   "hbm_frac": hot_gbs / (measured_peaks().get("hbm_gbs") or 6800.0),
                    "includes": "fluence readout, run labelling, union-find merge, roots, spread; count to host"}
 
         # ---- effective lens (Eqs. 4-6) and a turbulent layer (Eqs. 9-10) on the marched field
@@ -477,8 +481,17 @@ def main():
                 h1.record(stream)
                 torch.cuda.synchronize(dev)
                 tt.append(h0.elapsed_time(h1))
+            # HBM sweeps of the implementation, bytes per point (FP32 grid): lens 196
+            # (readout 16, fluence 16, DFT pair and filter 80, labelling 28, centres 36,
+            # reload 16, plus the screen near the lenses), layer 104 (readout 16,
+            # spectrum 16, inverse DFT 32, phase 24, reload 16)
+            pk_gbs = measured_peaks().get("hbm_gbs") or 6800.0
+            lens_gbs = 196.0 * n * n / (min(tl) / 1e3) / 1e9
+            turb_gbs = 104.0 * n * n / (min(tt) / 1e3) / 1e9
             lens_t = {"effective_lens_ms": min(tl), "lenses": nlens, "w_l_w_per_cm2": lens["w_l"],
                       "l_dif_cm2": lens["l_dif"], "turbulent_layer_ms": min(tt),
+                      "lens_sweep_gbs": lens_gbs, "lens_hbm_frac": lens_gbs / pk_gbs,
+                      "layer_sweep_gbs": turb_gbs, "layer_hbm_frac": turb_gbs / pk_gbs,
                       "includes": "lens: readout, low-pass DFT pair, labelling, centres, ansatz sum, reload; "
                                   "layer: readout, spectrum, inverse DFT pair, phase, reload"}
 
