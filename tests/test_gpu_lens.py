@@ -156,3 +156,22 @@ def test_lens_argument_errors():
         with pytest.raises(capi.NlseError) as ei:
             capi.nlse_effective_lens(g.h, capi.make_lens(LENS), small.data_ptr(), need // 2, 0, 0, 0)
         assert ei.value.status == capi.NLSE_ENOMEM
+
+
+def test_lens_fp32_full_size_4096():
+    """The dense-grid size (4096^2 FP32, 8 cm window): low-pass, centres (bit
+    for bit on the GPU's w_dif) and screen against the oracle."""
+    cfg = configs.cfg_dense_fp32()
+    n = cfg["n"]
+    U0 = spotted_field(n, cfg["L"], 40, 99).astype(np.complex64)
+    with Grid(cfg, precision="fp32") as g:
+        g.load(U0)
+        before = g.field()
+        k, cent, wd = g.effective_lens(LENS, w_dif=True)
+        after = g.field()
+    wd = wd.cpu().numpy()
+    wref = oracle.lens_lowpass(np.abs(before.astype(np.complex128)) ** 2, cfg["L"], LENS["l_dif"])
+    assert np.max(np.abs(wd - wref)) <= 1e-5 * np.max(wref)
+    cref = oracle.lens_centres(wd, float(np.float32(LENS["w_l"])), 4)
+    assert k == len(cref) and np.array_equal(cent, cref) and k >= 20
+    assert rel_l2(after, oracle.lens_apply(before, cfg["L"], cent, LENS)) <= 2e-6

@@ -115,3 +115,20 @@ def test_degenerate_layers_leave_the_field():
         for args in ((tau, kh, 0.0), (0.0, kh, thick), (tau, 0.5 * 2 * math.pi / cfg["L"], thick)):
             U = g.load(U0).turbulent_screen(xi, *args).field()
             assert rel_l2(U, U0) <= 1e-13
+
+
+def test_layer_fp32_full_size_4096():
+    """The dense-grid size (4096^2 FP32, 8 cm window, as the benchmark runs it):
+    the layer against the oracle on the whole field."""
+    cfg = configs.cfg_dense_fp32()
+    n = cfg["n"]
+    kunit = 2 * math.pi / cfg["L"]
+    k0 = 2 * math.pi * cfg["n0"] / cfg["lambda0"]
+    kh = 40.3 * kunit
+    tau = 2 * k0 / 50.0 / math.sqrt(math.pi * 40.3 ** 2)
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    xi = beams.turbulence_draws(n, 77).astype(np.complex64)
+    ref = oracle.turbulent_screen(U0, xi, cfg, tau, kh, 50.0)
+    with Grid(cfg, precision="fp32") as g:
+        U = g.load(U0).turbulent_screen(xi, tau, kh, 50.0).field()
+    assert rel_l2(U, ref) <= 2e-6
