@@ -1,7 +1,7 @@
 """Physical parameters and the five workloads of the split-step NLSE march.
 
 Plain numbers only: no arithmetic of the method lives here.  The values that
-the paper does not print are readings, listed with their reasons in the design doc:
+the paper does not print are readings of it:
 
 * carrier wavelength 800 nm (Sec. 2, below Eq. 1), n0 = 1, air n2 = 3.2e-19 cm^2/W;
 * multiphoton order K = 8 (Eq. 3 "m-th order"; O2 at 800 nm);
