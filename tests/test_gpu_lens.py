@@ -118,12 +118,14 @@ def test_degenerate_lenses():
     assert np.max(np.abs(after[n // 2:] - edge[n // 2:])) <= 1e-6  # rows beyond the reach: only the round trip
 
 
-def test_march_lens_march_fp64():
+@pytest.mark.parametrize("scheme", ["lie", "strang"])
+def test_march_lens_march_fp64(scheme):
     """The method's use: march to the pre-filamentation level, replace the
     filament region by the lens screen, march on; step count and history
-    continue across the screen."""
+    continue across the screen (Lie or symmetric steps around it)."""
     n = 256
     cfg = configs.physics(n, 1.28, 0.5, configs.ALL_TERMS)
+    cfg["scheme"] = scheme
     U0 = spotted_field(n, cfg["L"], 6, 9)
     lens = dict(LENS, w_l=5e11)
     a, _, _ = oracle.march(U0, cfg, 10, record=False)
