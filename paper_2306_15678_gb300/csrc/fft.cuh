@@ -64,6 +64,41 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
     return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// FP32 complex sums and differences as packed FP32x2 operations (one
+// instruction for both parts; each part rounds as a scalar add would)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// packed FP32x2 multiply and fused multiply-add, part by part
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+        "fma.rn.f32x2 pr, pa, pb, pc;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
     return mk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
@@ -177,6 +212,39 @@ template <int J, bool INV, typename V> __device__ __forceinline__ V w16(V a) {
     }
 }
 
+// FP32 forward W_16^J with packed parts: the same fused operations, in the
+// same order, as the scalar mulc / dotc forms above (the transforms of the
+// march run forward only; the inverse takes the generic form)
+template <int J, bool INV> __device__ __forceinline__ float2 w16(float2 a) {
+    constexpr int j = J & 15;
+    if constexpr (INV || j == 0 || j == 4 || j == 8 || j == 12) {
+        return w16<J, INV, float2>(a);
+    } else {
+        constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173,
+                         r2 = 0.70710678118654752440;
+        if constexpr ((j & 1) == 0) {
+            constexpr int cx = (j == 2 || j == 14) ? 1 : -1;
+            constexpr int sx = (j == 2 || j == 6) ? 1 : -1;
+            const float2 q = mk<float2>(cx * a.x + sx * a.y, cx * a.y - sx * a.x);
+            constexpr float h = (float)r2, l = (float)(r2 - (double)(float)r2);
+            return fma2(q, mk<float2>(h, h), mul2(q, mk<float2>(l, l)));
+        } else {
+            constexpr double c = j == 1 ? c1 : j == 3 ? s1 : j == 5 ? -s1 : j == 7 ? -c1
+                               : j == 9 ? -c1 : j == 11 ? -s1 : j == 13 ? s1 : c1;
+            constexpr double sn = j == 1 ? s1 : j == 3 ? c1 : j == 5 ? c1 : j == 7 ? s1
+                                : j == 9 ? -s1 : j == 11 ? -c1 : j == 13 ? -c1 : -s1;
+            constexpr float ch = (float)c, cl = (float)(c - (double)(float)c);
+            constexpr float sh = (float)sn, sl = (float)(sn - (double)(float)sn);
+            // re = dotc(x, c, y, sn), im = dotc(y, c, x, -sn): lanes (x, y) and (y, x)
+            const float2 A = a, S = mk<float2>(a.y, a.x);
+            float2 p = mul2(S, mk<float2>(sl, -sl));
+            p = fma2(A, mk<float2>(cl, cl), p);
+            p = fma2(S, mk<float2>(sh, -sh), p);
+            return fma2(A, mk<float2>(ch, ch), p);
+        }
+    }
+}
+
 // ----------------------------------------------------------------- DFT_R --
 
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a0, V& a1) {
@@ -192,6 +260,22 @@ template <bool INV, typename V> __device__ __forceinline__ void dft4(V& a0, V& a
     a2 = csub(t0, t2);
     a1 = cadd(t1, t3);
     a3 = csub(t1, t3);
+}
+
+// FP32: the four sums and differences of equal sign packed; the two outputs
+// that take the rotated difference mix sums and differences part by part and
+// stay scalar (same operations, same results as the generic form)
+template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    if constexpr (INV) {
+        a1 = mk<float2>(t1.x - d.y, t1.y + d.x);
+        a3 = mk<float2>(t1.x + d.y, t1.y - d.x);
+    } else {
+        a1 = mk<float2>(t1.x + d.y, t1.y - d.x);
+        a3 = mk<float2>(t1.x - d.y, t1.y + d.x);
+    }
 }
 
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V (&a)[R]) {
