@@ -150,10 +150,7 @@ __device__ __forceinline__ float2 apply_screen(float2 v, const ScreenCoef<float>
     // first-order part would lose it at every step, coherently
     const float ddx = fmaf(v.x, dre, -v.y * dim);
     const float ddy = fmaf(v.x, dim, v.y * dre);
-    float2 r;
-    r.x = v.x + ddx;
-    r.y = v.y + ddy;
-    return r;
+    return cadd(v, mk<float2>(ddx, ddy));
 }
 
 // FP64: the factor exp(re) (cos im + i sin im) directly
