@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-strang", action="store_true")
     ap.add_argument("--no-hot", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
-    ap.add_argument("--large-adjoint-steps", type=int, default=100)
+    ap.add_argument("--large-adjoint-steps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -114,71 +114,169 @@ def measured_peaks() -> dict:
 
 
 class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the SM clock, power and throttle
+    reasons, each stamped with its arrival time, so that the samples taken
+    while a given window of work ran can be picked out afterwards."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
+        import threading
         self.proc = None
-        self.path = None
+        self.rows = []  # (arrival time, fields)
+        self.error = None
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)], stdout=self.out, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
+                 "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                text=True)
+        except Exception as e:  # no nvidia-smi on this host
+            self.error = f"nvidia-smi not started: {e}"
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
 
-    def stop(self) -> dict | None:
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.perf_counter(), parts))
+            elif line.strip():
+                self.error = f"unexpected nvidia-smi line: {line.strip()[:120]}"
+
+    def wait_for_samples(self, k: int, timeout: float = 3.0, busy=None):
+        """Run busy() (work on the GPU) until k more samples have arrived."""
+        target = len(self.rows) + k
+        t0 = time.perf_counter()
+        while len(self.rows) < target and time.perf_counter() - t0 < timeout and self.proc is not None:
+            if busy is not None:
+                busy()
+            else:
+                time.sleep(0.02)
+
+    def stop(self, t_lo: float, t_hi: float) -> dict | None:
+        """Summary of the samples that arrived between t_lo and t_hi (perf_counter)."""
         if self.proc is None:
-            return None
+            return {"error": self.error} if self.error else None
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.out.close()
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        self.thread.join(timeout=2)
+        if not self.rows:
+            err = self.error or (self.proc.stderr.read()[:200] if self.proc.stderr else "")
+            return {"error": f"no samples: {err}".strip()}
+        rows = [r for t, r in self.rows if t_lo <= t <= t_hi]
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for _, r in self.rows if num(r[2])]
+        pw = [float(r[3]) for r in rows if num(r[3])]
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
-            for nm, v in zip(names, r[5:9]):
+            for nm, v in zip(self.NAMES, r[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(cfg, U0, seconds: float) -> dict:
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of
-    the same workload: whole oracle z steps of the full grid until ~seconds."""
+    the same workload: whole oracle z steps of the full grid, about 60 % of
+    `seconds` on every core and the rest on one core."""
     import oracle
+
+    def timed(budget: float, max_steps: int):
+        U = U0
+        steps = 0
+        t0 = time.perf_counter()
+        while True:
+            U, _, _ = oracle.march(U, cfg, 1, record=False)
+            steps += 1
+            if time.perf_counter() - t0 >= budget or steps >= max_steps:
+                break
+        return steps, time.perf_counter() - t0
+
     n = cfg["n"]
-    U = U0
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        U, _, _ = oracle.march(U, cfg, 1, record=False)
-        steps += 1
-        if time.perf_counter() - t0 >= seconds or steps >= 50:
+    cores = oracle.num_threads()
+    steps, dt = timed(0.6 * seconds, 50)
+    oracle.set_num_threads(1)
+    try:
+        steps1, dt1 = timed(0.4 * seconds, 20)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": n * n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"{steps} full z steps of the {n}x{n} workload in FP64 on {cores} threads ({dt:.1f} s)",
+            "one_core": {"value": n * n * steps1 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"{steps1} full z steps on 1 thread ({dt1:.1f} s)"}}
+
+
+def alu_peak(kind: int, dev, stream) -> float:
+    """Peak fused multiply-add rate (FMAs/s, lanes counted) of the GPU for kind
+    0 FP32, 1 FP64, 2 packed FP32x2, from the library's probe kernel timed with
+    CUDA events on its stream; the launch is scaled to run >= 30 ms."""
+    import torch
+
+    from paper_2306_15678_gb300 import capi
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    sink = torch.zeros(blocks, dtype=torch.float64, device=dev)
+    lanes = 2 if kind == 2 else 1
+
+    def run(iters: int) -> float:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        capi.nlse_alu_probe(kind, iters, blocks, stream.cuda_stream, sink.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    iters = 256
+    for _ in range(24):
+        ms = run(iters)
+        if ms >= 30.0 or iters >= (1 << 28):
             break
-    dt = time.perf_counter() - t0
-    return {"value": n * n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} full z steps of the {n}x{n} workload in FP64 ({dt:.1f} s)"}
+        iters = int(iters * (40.0 / ms if ms > 1.0 else 8.0))
+    fmas = blocks * 256 * 8 * lanes * iters
+    return max(fmas / (run(iters) / 1e3) for _ in range(3))
+
+
+def fp64_ops_per_point_step() -> dict | None:
+    """FP64 arithmetic instructions (per lane) per grid point and z step of the
+    FP64 march at 4096^2, from the ncu capture summarised in profiles/ (valid
+    while the march sources are unchanged)."""
+    path = os.path.join(ROOT, "profiles", "fp64_march_ops.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    return d if d.get("csrc_digest") == csrc_digest() else None
 
 
 def traffic_for(kernel_key: str) -> float | None:
@@ -280,10 +378,13 @@ def bench_adjoint(dev) -> dict:
 
 
 def bench_large_adjoint(dev, nsteps: int) -> dict:
-    """A sample of the large batched adjoint: one of its 8192^2 beams (16 cm
-    window, w0 = 3 cm, P = 500 P_cr, full screen), nsteps steps with
-    ceil(sqrt(nsteps)) checkpointing, FP32 field, FP64 loss and gradients;
-    against the plain forward march of the same steps."""
+    """One beam of the large batched adjoint: an 8192^2 grid (16 cm window,
+    w0 = 3 cm, P = 500 P_cr, full screen), nsteps steps (3000: the whole
+    march) with ceil(sqrt(nsteps)) checkpointing, FP32 field, FP64 loss and
+    gradients; against the plain forward march of the same steps.  The input
+    field is resident on the device for both, and both are timed with CUDA
+    events on the march's stream (the adjoint forward ends with the loss
+    readout, which synchronises)."""
     import time
 
     import numpy as np
@@ -295,34 +396,49 @@ def bench_large_adjoint(dev, nsteps: int) -> dict:
     cfg = configs.cfg_large_adjoint(1)[0]
     n = cfg["n"]
     k = configs.sqrt_checkpoint(nsteps)
-    U0 = beams.make_field(cfg).astype(np.complex64)
-    D = np.abs(beams.make_field(dict(cfg, beam=dict(cfg["beam"], w0=3.06, seed=5099)))) ** 2
-    with Grid(cfg, precision="fp32", device=dev) as g:
-        g.load(U0).step(3)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        g.step(nsteps)
-        g.power()
-        fwd = time.perf_counter() - t0
-    fit = AdjointMarch(cfg, nsteps, k, precision="fp32", device=dev)
-    try:
-        fit.set_target(D)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        J = fit.forward(U0)
-        t1 = time.perf_counter()
-        dth, _ = fit.backward()
-        torch.cuda.synchronize(dev)
-        t2 = time.perf_counter()
-        ws = fit.ws_bytes
-    finally:
-        fit.close()
+    stream = torch.cuda.Stream(device=dev)
+    U0 = torch.from_numpy(beams.make_field(cfg).astype(np.complex64)).to(dev)
+    D = torch.from_numpy(np.abs(beams.make_field(dict(cfg, beam=dict(cfg["beam"], w0=3.06, seed=5099)))) ** 2).to(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        with Grid(cfg, precision="fp32", device=dev, stream=stream) as g:
+            g.load(U0).step(3)
+            g.load(U0)
+            torch.cuda.synchronize(dev)
+            f0, f1 = ev(), ev()
+            f0.record(stream)
+            g.step(nsteps)
+            f1.record(stream)
+            p_end = g.power()
+            fwd_ms = f0.elapsed_time(f1)
+        fit = AdjointMarch(cfg, nsteps, k, precision="fp32", device=dev, stream=stream)
+        try:
+            fit.set_target(D)
+            torch.cuda.synchronize(dev)
+            a0, a1, a2 = ev(), ev(), ev()
+            t0 = time.perf_counter()
+            a0.record(stream)
+            J = fit.forward(U0)
+            a1.record(stream)
+            dth, dU = fit.backward()
+            a2.record(stream)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t0
+            afwd_ms, abwd_ms = a0.elapsed_time(a1), a1.elapsed_time(a2)
+            ws = fit.ws_bytes
+            dU_finite = bool(torch.isfinite(torch.view_as_real(dU)).all())
+        finally:
+            fit.close()
     return {"workload": f"1 of 8 beams {n}x{n}, {nsteps} of 3000 steps, checkpoint every {k} (sqrt), FP32, "
-                        "6 gains + input field",
-            "forward_march_ms": fwd * 1e3, "adjoint_forward_ms": (t1 - t0) * 1e3,
-            "adjoint_backward_ms": (t2 - t1) * 1e3, "adjoint_over_forward": (t2 - t0) / fwd,
-            "gradient_pt_steps_per_s": n * n * nsteps / (t2 - t0), "workspace_gib": ws / 2 ** 30,
-            "loss": J, "grad_finite": bool(np.all(np.isfinite(dth)))}
+                        "6 gains + input field; input field resident on the device",
+            "steps": nsteps, "checkpoint_every": k,
+            "forward_march_ms": fwd_ms, "adjoint_forward_ms": afwd_ms, "adjoint_backward_ms": abwd_ms,
+            "adjoint_over_forward": (afwd_ms + abwd_ms) / fwd_ms,
+            "backward_over_forward": abwd_ms / fwd_ms,
+            "forward_pt_steps_per_s": n * n * nsteps / (fwd_ms / 1e3),
+            "gradient_pt_steps_per_s": n * n * nsteps / ((afwd_ms + abwd_ms) / 1e3),
+            "adjoint_wall_s": wall, "workspace_gib": ws / 2 ** 30, "final_power_w": p_end,
+            "loss": J, "grad_finite": bool(np.all(np.isfinite(dth))) and dU_finite}
 
 
 def run_reference(args, world, rank, cfg):
@@ -352,8 +468,9 @@ def run_reference(args, world, rank, cfg):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
         "steps": k, "warmup": warm, "ms_per_step": dt * 1e3 / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_desc(cfg),
+        "data": "synthetic", "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "cpu": cpu_model(),
                          "sample": f"{k} of {args.steps} requested z steps of the {n}x{n} workload "
                                    f"(time budget {args.ref_budget:.0f} s)"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -398,8 +515,25 @@ def main():
             if dist is not None:
                 dist.barrier()
 
-        # ---- timed region: K z steps, CUDA events on the grid's stream
+        # ---- clocks: nvidia-smi samples every 200 ms, so a timed region of a few
+        # milliseconds falls between two samples; the same march runs on a second
+        # grid for >= 3 samples right before and right after the timed region,
+        # and the samples of that whole window are reported
         clocks = ClockSampler(local)
+        g_clk = Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream)
+        capi.nlse_set_column_tile(g_clk.h, cols)
+        g_clk.load(U0)
+
+        def busy():
+            g_clk.step(100)
+            torch.cuda.synchronize(dev)
+
+        busy()
+        clocks.wait_for_samples(1, timeout=5.0, busy=busy)
+        t_lo = time.perf_counter()
+        clocks.wait_for_samples(3, timeout=3.0, busy=busy)
+
+        # ---- timed region: K z steps, CUDA events on the grid's stream
         barrier()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -410,7 +544,13 @@ def main():
         torch.cuda.synchronize(dev)
         barrier()
         ms = e0.elapsed_time(e1)
-        clk = clocks.stop()
+        clocks.wait_for_samples(3, timeout=3.0, busy=busy)
+        t_hi = time.perf_counter()
+        clk = clocks.stop(t_lo, t_hi)
+        if clk is not None:
+            clk["window"] = (f"the timed region plus the same march on a second grid for {t_hi - t_lo:.2f} s "
+                             "around it (samples every 200 ms)")
+        g_clk.close()
         # replicas: sum of every rank's point-steps over the slowest rank's time
         value, ms = shard.aggregate(float(n * n * args.steps), ms, dist, dev)
 
@@ -532,8 +672,21 @@ def main():
             torch.cuda.synchronize(dev)
             ms64 = a0.elapsed_time(a1)
             v64 = n * n * k64 / (ms64 / 1e3)
-            fp64 = {"value": v64, "unit": UNIT, "steps": k64, "fp32_over_fp64": value / world / v64}
             g64.close()
+            fma64 = alu_peak(1, dev, stream)
+            fma32 = alu_peak(0, dev, stream)
+            ops = fp64_ops_per_point_step()
+            fp64 = {"value": v64, "unit": UNIT, "steps": k64, "fp32_over_fp64": value / world / v64,
+                    "hbm_frac": 64.0 * v64 / (peak_gbs * 1e9),
+                    "fp64_fma_peak_per_s": fma64, "fp32_fma_peak_per_s": fma32,
+                    "fp64_over_fp32_fma_rate": fma64 / fma32 if fma32 else None}
+            if ops and fma64:
+                # FP64 pipe: every DFMA, DMUL and DADD takes one issue slot of the FP64
+                # pipe, which the probe fills with DFMA alone
+                per = float(ops["fp64_inst_per_point_step"])
+                fp64["alu"] = {"bound": "alu", "fp64_inst_per_point_step": per,
+                               "achieved": per * v64, "peak": fma64, "unit": "FP64 inst/s",
+                               "frac": per * v64 / fma64, "source": ops.get("source")}
 
         # ---- end to end through the public API with host buffers
         e2e = None
@@ -570,7 +723,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}", column_tile=cols),
+            "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
+            "launch": {"column_tile": cols, "column_tile_source": "autotuner (tune.tune_grid)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
             "strang": strang, "hot_areas": hot, "lens_and_turbulence": lens_t, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,

@@ -153,6 +153,17 @@ nlse_status nlse_step(nlse_grid* g, int32_t nsteps);
  * for the per-kernel roofline; the paper has no counterpart. */
 nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double* row_ms);
 
+/* Arithmetic-rate probe: enqueue on cuda_stream one launch of `blocks` blocks
+ * of 256 threads, every thread running 8 independent fused multiply-add
+ * chains for `iters` rounds: kind 0 = FP32 FMA, 1 = FP64 FMA, 2 = packed
+ * FP32x2 FMA (fma.rn.f32x2, two FMAs per instruction).  The caller times the
+ * launch (CUDA events on the same stream) to get the peak FMA rate, the
+ * denominator of the ALU roofline of the FP64 march.  sink_dev: device
+ * buffer of `blocks` 8-byte slots (8-byte aligned) that the kernel may write.
+ * NLSE_EINVAL for iters < 1, blocks < 1, a null or misaligned sink or an
+ * unknown kind.  Measurement aid; the paper has no counterpart. */
+nlse_status nlse_alu_probe(int32_t kind, int32_t iters, int32_t blocks, void* cuda_stream, void* sink_dev);
+
 /* Column tile of the column pass: a width of 1, 2, 4, 8 or 16 columns per
  * block, or'ed with NLSE_COL_TMA for the variant that moves the tile between
  * global and shared memory with bulk tensor copies (cp.async.bulk.tensor,
@@ -163,7 +174,11 @@ nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double
  * NLSE_EUNSUPPORTED for a tile this size cannot use.  Chosen by the
  * autotuner; results do not depend on it, bit for bit.  A bounded wait (1 s)
  * of the staged variant that runs out makes the block skip its tile and sets
- * NLSE_ETIMEOUT in the device status word (nlse_device_status). */
+ * NLSE_ETIMEOUT in the device status word (nlse_device_status).  The block
+ * then waits once more (1 s) for the copy it started; if that copy still has
+ * not landed, it may land later in shared memory of another block, so after
+ * an NLSE_ETIMEOUT the field of the grid and the results of later kernels on
+ * its stream are not to be trusted: destroy the grid and reload. */
 enum { NLSE_COL_TMA = 0x100 };
 nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols);
 
@@ -300,10 +315,12 @@ nlse_status nlse_device_status(nlse_grid* g);
  * pool at start-up, or a loop that cannot afford the device-wide
  * synchronisation cudaMalloc/cudaFree can cause.
  *   field_dev: device pointer, n x n interleaved complex of `precision`
- *              (physical field U, row-major), read only;
+ *              (physical field U, row-major), read only; aligned to one
+ *              complex value (16 bytes in FP64, 8 in FP32), else NLSE_EINVAL;
  *   n:         1 <= n <= 8192 rows and columns; larger n returns
  *              NLSE_EUNSUPPORTED before any launch;
- *   out_dev:   device pointer to 2 doubles, receives (power, peak).
+ *   out_dev:   device pointer to 2 doubles (8-byte aligned, else NLSE_EINVAL),
+ *              receives (power, peak).
  * Enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream);
  * does not synchronise.  The per-row partial sums live in one 128 KiB
  * __device__ array that every device loading the library keeps until exit and

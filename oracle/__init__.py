@@ -113,6 +113,7 @@ def _configure(lib):
     cp = ctypes.c_void_p
     P = ctypes.POINTER(OrcParams)
     lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     lib.orc_fft1d.argtypes = [cp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.orc_fft2d.argtypes = [cp, ctypes.c_int, ctypes.c_int]
     lib.orc_propagator.argtypes = [P, cp]
@@ -193,6 +194,11 @@ def _c128(a) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads the oracle's parallel loops use from now on in this thread."""
+    _load().orc_set_num_threads(int(k))
 
 
 def fft1(a, inverse: bool = False) -> np.ndarray:

@@ -91,6 +91,17 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel loops of the calling thread (timing of
+ * the oracle on fewer cores; the arithmetic and its order do not depend on it:
+ * every parallel loop writes disjoint outputs and the sums are serial). */
+void orc_set_num_threads(int k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* ------------------------------------------------------------------ FFT -- */
 
 /* twiddle table tw[j] = exp(-2 pi i j / n), j < n/2 */

@@ -106,6 +106,8 @@ _SIGS = {
     "nlse_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "nlse_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "nlse_alu_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "nlse_steps_taken": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "nlse_power": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "nlse_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -216,6 +218,14 @@ def nlse_step_timed(h, nsteps: int) -> tuple[float, float]:
     r = ctypes.c_double(0.0)
     check(lib().nlse_step_timed(h, int(nsteps), ctypes.byref(c), ctypes.byref(r)), "nlse_step_timed")
     return float(c.value), float(r.value)
+
+
+def nlse_alu_probe(kind: int, iters: int, blocks: int, stream: int, sink_dev: int) -> None:
+    """Enqueue the FMA-rate probe (kind 0 FP32, 1 FP64, 2 packed FP32x2):
+    blocks x 256 threads x 8 chains x iters fused multiply-adds (x 2 lanes for
+    kind 2)."""
+    check(lib().nlse_alu_probe(int(kind), int(iters), int(blocks), ctypes.c_void_p(stream),
+                               ctypes.c_void_p(sink_dev)), "nlse_alu_probe")
 
 
 def nlse_steps_taken(h) -> int:

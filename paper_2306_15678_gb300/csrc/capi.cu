@@ -1039,7 +1039,7 @@ nlse_status nlse_device_status(nlse_grid* g) {
         return NLSE_ECUDA;
     if (cudaMemsetAsync(g->ws + g->lay.status, 0, sizeof(int), g->stream) != cudaSuccess) return NLSE_ECUDA;
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) return NLSE_ECUDA;
-    if (word & 2) return NLSE_ETIMEOUT;
+    if (word & 6) return NLSE_ETIMEOUT;
     if (word & 1) return NLSE_ENONFINITE;
     return NLSE_OK;
 }

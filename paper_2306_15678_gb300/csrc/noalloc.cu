@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/nlse.h"
@@ -107,6 +108,10 @@ extern "C" nlse_status nlse_power_peak_noalloc(const void* field_dev, int32_t n,
                                                double L, void* cuda_stream, double* out_dev) {
     if (!field_dev || !out_dev) return NLSE_EINVAL;
     if (n < 1 || !(L > 0.0) || !std::isfinite(L)) return NLSE_EINVAL;
+    // the kernels read whole complex values (16 bytes in FP64, 8 in FP32) and
+    // store doubles: a misaligned pointer is refused here, not faulted on
+    const uintptr_t fa = reinterpret_cast<uintptr_t>(field_dev), oa = reinterpret_cast<uintptr_t>(out_dev);
+    if ((fa % (precision == NLSE_FP64 ? 16u : 8u)) != 0 || (oa % 8u) != 0) return NLSE_EINVAL;
     if (n > kNoallocMaxRows) return NLSE_EUNSUPPORTED;  // beyond the static scratch
     if (precision != NLSE_FP64 && precision != NLSE_FP32) return NLSE_EUNSUPPORTED;
     double* rows = nullptr;

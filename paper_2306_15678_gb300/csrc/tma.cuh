@@ -16,7 +16,11 @@
 //
 // Waits are bounded by a %globaltimer deadline: on expiry the block records
 // bit 1 (NLSE_ETIMEOUT) in the status word, waits once more, bounded, for the
-// copy it started, and returns without touching the field.  Bulk tensor
+// copy it started, and returns without touching the field.  If that second
+// wait runs out too, the copy may still be in flight into shared memory that
+// a later block can be given: the block also sets bit 2, which the host
+// reports as NLSE_ETIMEOUT as well and which means that the output of this
+// launch and of every later kernel on the stream is not to be trusted.  Bulk tensor
 // copies need a 128-byte aligned shared-memory address; dynamic shared memory
 // is only guaranteed 16 bytes, so the launch adds kTmaAlignPad bytes and the
 // kernel aligns the base at run time.
@@ -142,7 +146,8 @@ k_col_pass_tma(const __grid_constant__ CUtensorMap mload, const __grid_constant_
             tma_load_3d(stage + b * kTmaBoxRows * C * 2, &mload, 0, col0, b * kTmaBoxRows, &bar);
         if (!mbar_wait_bounded(&bar, 0)) {
             if (status) atomicOr(status, 2);
-            mbar_wait_bounded(&bar, 0);  // the copy still targets this block's memory
+            // the copy still targets this block's memory: wait for it once more
+            if (!mbar_wait_bounded(&bar, 0) && status) atomicOr(status, 4);
             s_fail = 1;
         }
     }
