@@ -98,7 +98,7 @@ def csrc_digest() -> str:
     while this digest is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2306_15678_gb300", "csrc")
-    for fn in ("dispatch.cuh", "fft.cuh", "kernels.cuh", "tma.cuh"):
+    for fn in ("dispatch.cuh", "dispatch32.cuh", "fft.cuh", "kernels.cuh", "pair.cuh", "pass32.cuh", "tma.cuh"):
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -262,6 +262,7 @@ def alu_peak(kind: int, dev, stream) -> float:
         if ms >= 30.0 or iters >= (1 << 28):
             break
         iters = int(iters * (40.0 / ms if ms > 1.0 else 8.0))
+    iters = (iters + 15) // 16 * 16  # the kernel runs whole trips of 16 rounds
     fmas = blocks * 256 * 8 * lanes * iters
     return max(fmas / (run(iters) / 1e3) for _ in range(3))
 
@@ -501,9 +502,10 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     from paper_2306_15678_gb300 import capi, shard, tune
     with torch.cuda.stream(stream):
-        cols = tune.tune_grid(cfg, "fp32", steps=10)
+        launch = tune.tune_launch(cfg, "fp32", steps=10)
+        cols = launch["cols"]
         g = Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream)
-        capi.nlse_set_column_tile(g.h, cols)
+        tune.apply_launch(g, launch)
         g.load(U0)
         g.step(max(args.warmup, 3))
         torch.cuda.synchronize(dev)
@@ -521,7 +523,7 @@ def main():
         # and the samples of that whole window are reported
         clocks = ClockSampler(local)
         g_clk = Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream)
-        capi.nlse_set_column_tile(g_clk.h, cols)
+        tune.apply_launch(g_clk, launch)
         g_clk.load(U0)
 
         def busy():
@@ -568,9 +570,10 @@ def main():
         peak_gbs = peak_gbs or 6800.0
         achieved = bytes_launch / (dom_ms / 1e3) / 1e9
         if dom == "column pass":
-            kkey = f"{'k_col_pass_tma' if cols & capi.NLSE_COL_TMA else 'k_col_pass'}<float,{n},{cols & 0xff}>"
+            radix = 8 if cols & capi.NLSE_COL_R8 else 16
+            kkey = f"{'k_col_pass32_tma' if cols & capi.NLSE_COL_TMA else 'k_col_pass32'}<{n},{radix},{cols & 0xff}>"
         else:
-            kkey = f"k_row_pass<float,{n},diag>"
+            kkey = f"k_row_pass32<{n},{launch['row_radix']},diag>"
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                     "frac": achieved / peak_gbs, "traffic": traffic_for(kkey),
                     "kernel": dom, "kernel_ms": dom_ms,
@@ -639,7 +642,7 @@ def main():
         strang = None
         if not args.no_strang:
             gs = Grid(dict(cfg, scheme="strang"), precision="fp32", diag_every=1, device=dev, stream=stream)
-            capi.nlse_set_column_tile(gs.h, cols)
+            tune.apply_launch(gs, launch)
             gs.load(U0)
             gs.step(3)
             ks = max(50, min(args.steps // 4, 500))
@@ -675,10 +678,12 @@ def main():
             g64.close()
             fma64 = alu_peak(1, dev, stream)
             fma32 = alu_peak(0, dev, stream)
+            fma32x2 = alu_peak(2, dev, stream)
             ops = fp64_ops_per_point_step()
             fp64 = {"value": v64, "unit": UNIT, "steps": k64, "fp32_over_fp64": value / world / v64,
                     "hbm_frac": 64.0 * v64 / (peak_gbs * 1e9),
                     "fp64_fma_peak_per_s": fma64, "fp32_fma_peak_per_s": fma32,
+                    "fp32x2_fma_peak_per_s": fma32x2,
                     "fp64_over_fp32_fma_rate": fma64 / fma32 if fma32 else None}
             if ops and fma64:
                 # FP64 pipe: every DFMA, DMUL and DADD takes one issue slot of the FP64
@@ -724,7 +729,8 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_desc(cfg), parallelism=f"replicas x{world}"),
-            "launch": {"column_tile": cols, "column_tile_source": "autotuner (tune.tune_grid)"},
+            "launch": {"column_tile": cols, "row_radix": launch["row_radix"],
+                       "source": "autotuner (tune.tune_launch: column tile incl. its radix, then the row radix)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_march": fp64,
             "strang": strang, "hot_areas": hot, "lens_and_turbulence": lens_t, "batch": batch, "adjoint": adjoint, "large_adjoint": large_adjoint,

@@ -155,8 +155,9 @@ nlse_status nlse_step_timed(nlse_grid* g, int32_t nsteps, double* col_ms, double
 
 /* Arithmetic-rate probe: enqueue on cuda_stream one launch of `blocks` blocks
  * of 256 threads, every thread running 8 independent fused multiply-add
- * chains for `iters` rounds: kind 0 = FP32 FMA, 1 = FP64 FMA, 2 = packed
- * FP32x2 FMA (fma.rn.f32x2, two FMAs per instruction).  The caller times the
+ * chains for `iters` rounds (rounded up to a multiple of 16): kind 0 = FP32
+ * FMA, 1 = FP64 FMA, 2 = packed FP32x2 FMA (fma.rn.f32x2, two FMAs per
+ * instruction).  The caller times the
  * launch (CUDA events on the same stream) to get the peak FMA rate, the
  * denominator of the ALU roofline of the FP64 march.  sink_dev: device
  * buffer of `blocks` 8-byte slots (8-byte aligned) that the kernel may write.
@@ -167,20 +168,32 @@ nlse_status nlse_alu_probe(int32_t kind, int32_t iters, int32_t blocks, void* cu
 /* Column tile of the column pass: a width of 1, 2, 4, 8 or 16 columns per
  * block, or'ed with NLSE_COL_TMA for the variant that moves the tile between
  * global and shared memory with bulk tensor copies (cp.async.bulk.tensor,
- * boxes of 512 rows) instead of per-thread loads and stores; that variant
- * exists for n >= 512 (default there: one column per block).  The field
- * between the passes is stored with the two rows of each row pair interleaved
- * element by element, so that one column is a sequence of 16-byte units.
- * NLSE_EUNSUPPORTED for a tile this size cannot use.  Chosen by the
- * autotuner; results do not depend on it, bit for bit.  A bounded wait (1 s)
- * of the staged variant that runs out makes the block skip its tile and sets
- * NLSE_ETIMEOUT in the device status word (nlse_device_status).  The block
- * then waits once more (1 s) for the copy it started; if that copy still has
- * not landed, it may land later in shared memory of another block, so after
- * an NLSE_ETIMEOUT the field of the grid and the results of later kernels on
- * its stream are not to be trusted: destroy the grid and reload. */
-enum { NLSE_COL_TMA = 0x100 };
+ * boxes of 512 rows) instead of per-thread loads and stores (n >= 512), and
+ * in FP32 with NLSE_COL_R8 for the radix-8 column transform (8 elements per
+ * thread, more threads in flight, one more shared-memory exchange; radix 16
+ * without it).  The field between the passes is stored in 16-byte units that
+ * hold one column's values at two adjacent rows, so a column is a sequence of
+ * units.  NLSE_EUNSUPPORTED for a tile this size or precision cannot use.
+ * Chosen by the autotuner (default FP32: the narrowest radix-16 staged tile
+ * of at least 128 threads); for a given radix the results do not depend on
+ * the tile, bit for bit, while the radix changes the rounding (both stay
+ * within the stated tolerances).  A bounded wait (1 s) of the staged variant
+ * that runs out makes the block skip its tile and sets NLSE_ETIMEOUT in the
+ * device status word (nlse_device_status).  The block then waits once more
+ * (1 s) for the copy it started; if that copy still has not landed, it may
+ * land later in shared memory of another block, so after an NLSE_ETIMEOUT the
+ * field of the grid and the results of later kernels on its stream are not to
+ * be trusted: destroy the grid and reload. */
+enum { NLSE_COL_TMA = 0x100, NLSE_COL_R8 = 0x200 };
 nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols);
+
+/* Radix of the row pass's transforms: 16 (16 elements per thread, the default
+ * in FP32) or 8 (8 elements per thread: twice the threads in flight, one more
+ * shared-memory exchange per transform); FP64 grids take 8 only.
+ * NLSE_EUNSUPPORTED otherwise.  Chosen by the autotuner with the column tile;
+ * the radix changes the rounding, not the tolerances met.  Finalises pending
+ * diagnostics first (enqueued on the grid's stream). */
+nlse_status nlse_set_row_radix(nlse_grid* g, int32_t radix);
 
 /* Number of z steps taken since the last load. */
 nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps);

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libnlse.so")
 NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
 NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
 NLSE_COL_TMA = 0x100  # column tile staged with bulk tensor copies (or'ed with the width)
+NLSE_COL_R8 = 0x200  # radix-8 column transform (FP32; or'ed with the tile code)
 NLSE_LIE, NLSE_STRANG = 0, 1  # splitting of a step
 NLSE_EXACT_SCREEN = 2  # or'ed into the scheme: exact pointwise substep instead of the frozen screen
 NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15
@@ -142,6 +143,7 @@ _SIGS = {
     "nlse_batch_power": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "nlse_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "nlse_set_column_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "nlse_set_row_radix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "nlse_adjoint_workspace_size": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.POINTER(ctypes.c_size_t)]),
     "nlse_adjoint_create": (ctypes.c_int, [ctypes.POINTER(nlse_params), ctypes.c_int32, ctypes.c_int32,
@@ -359,6 +361,10 @@ def nlse_adjoint_destroy(h) -> None:
 
 def nlse_set_column_tile(h, cols: int) -> None:
     check(lib().nlse_set_column_tile(h, int(cols)), "nlse_set_column_tile")
+
+
+def nlse_set_row_radix(h, radix: int) -> None:
+    check(lib().nlse_set_row_radix(h, int(radix)), "nlse_set_row_radix")
 
 
 def _params_array(params):

@@ -13,9 +13,10 @@
 // NLSE_ETIMEOUT in the status word, raises an abort flag that stops every
 // other block, and returns.
 //
-// Tile bodies are the per-pass kernels' own (row_tile / col_tile), with field
-// accesses that bypass L1 because other SMs rewrite the fields during the
-// launch, so a batched beam is bit-identical to the same beam marched alone.
+// Tile bodies are the per-pass kernels' own (row_tile32 / col_tile32 of the
+// pair engine, radix 16), with field accesses that bypass L1 because other SMs rewrite
+// the fields during the launch, so a batched beam is bit-identical to the same
+// beam marched alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,7 +27,7 @@
 #include <vector>
 
 #include "../../include/nlse.h"
-#include "dispatch.cuh"
+#include "dispatch32.cuh"
 #include "host_detail.h"
 
 namespace nlse {
@@ -35,10 +36,10 @@ constexpr int kBatchMinLog2 = 8, kBatchMaxLog2 = 12;  // n = 256 .. 4096
 constexpr int kRotSteps = 1 << 20;  // steps covered by the per-step phase table
 
 struct BatchBeam {
-    float2* field;
-    const float2* px;  // kDither copies of n entries each (copy k mod kDither serves step k)
-    const float2* py;
-    const float2* tw;
+    float4* field;     // unit layout (pass32.cuh)
+    const float2* px;  // kDitherP copies of n entries each (copy k mod kDitherP serves step k)
+    const unsigned char* py;  // kDitherP copies of P_y and the cross-lane factors (py32_copy_bytes)
+    const unsigned char* tw;  // kDither twiddle blocks (pass32.cuh: tw32_copy_bytes)
     ScreenCoef<float> sc;
     int log2n;
     int col_tiles;
@@ -70,17 +71,20 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     return v;
 }
 
-// rows / columns per tile for a block of THREADS threads
-template <int THREADS, int N> __host__ __device__ constexpr int tile_lines() {
-    return THREADS / threads_per_line<float, N>();
+// row pairs / columns per tile for a block of THREADS threads
+template <int THREADS, int N> __host__ __device__ constexpr int tile_pairs() { return THREADS / p_tpl<N, 16>(); }
+template <int THREADS, int N> __host__ __device__ constexpr int tile_cols() { return THREADS / p_col_tpl<N, 16>(); }
+template <int THREADS, int N> __host__ __device__ constexpr int batch_row_smem() {
+    return pr::pair_line_stride<N, p_e<N, 16>(), tile_pairs<THREADS, N>()>() * tile_pairs<THREADS, N>() * 16;
 }
 template <int THREADS, int N> __host__ __device__ constexpr bool batch_supported() {
-    return threads_per_line<float, N>() <= THREADS && tile_lines<THREADS, N>() <= N &&
-           line_stride<float, N, tile_lines<THREADS, N>()>() * tile_lines<THREADS, N>() * 8 <= kMaxSmem;
+    return p_tpl<N, 16>() <= THREADS && p_col_tpl<N, 16>() <= THREADS && tile_pairs<THREADS, N>() <= N / 2 &&
+           tile_cols<THREADS, N>() <= N && batch_row_smem<THREADS, N>() <= kMaxSmem &&
+           p_col_smem<N, 16, tile_cols<THREADS, N>()>() <= kMaxSmem;
 }
 template <int THREADS, int N> __host__ __device__ constexpr int batch_smem() {
     if constexpr (batch_supported<THREADS, N>())
-        return line_stride<float, N, tile_lines<THREADS, N>()>() * tile_lines<THREADS, N>() * 8;
+        return std::max(batch_row_smem<THREADS, N>(), p_col_smem<N, 16, tile_cols<THREADS, N>()>());
     else
         return 0;
 }
@@ -92,24 +96,27 @@ template <int THREADS> constexpr int batch_smem_max() {
 // one tile of global step k with the step's table copy, as a single grid applies it
 template <int THREADS, int N>
 __device__ __forceinline__ void batch_tile(const BatchBeam& bm, bool col, int tile, long long k, float2 rot,
-                                           float2* smem) {
+                                           C2* smem) {
     if constexpr (batch_supported<THREADS, N>()) {
-        constexpr int L = tile_lines<THREADS, N>();
-        const size_t copy = (size_t)(k & (kDither - 1)) * N;
-        const float2* tw = bm.tw + copy;
+        const int d = (int)(k & (kDither - 1)), dp = (int)(k & (kDitherP - 1));
+        const unsigned char* twb = bm.tw + (size_t)d * tw32_copy_bytes(N);
         if (col) {
-            col_tile<float, N, L, MemCG>(bm.field, bm.field, tw, bm.px + copy, bm.py + copy, rot, tile * L, smem);
+            constexpr int C = tile_cols<THREADS, N>();
+            col_tile32<N, 16, C, UnitCG>(bm.field, bm.field, twb, bm.px + (size_t)dp * N,
+                                         reinterpret_cast<const float4*>(bm.py + (size_t)dp * py32_copy_bytes(N)),
+                                         rot, tile * C, smem);
         } else {
+            constexpr int RP = tile_pairs<THREADS, N>();
             float ts = 0.f, tm = 0.f;
-            row_tile<float, N, L, false, MemCG>(bm.field, bm.field, tw, bm.sc, tile * L, smem, ts, tm);
+            row_tile32<N, 16, RP, false, UnitCG>(bm.field, bm.field, twb, bm.sc, tile * RP, smem, ts, tm);
         }
     }
 }
 
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, min_blocks<THREADS>()) k_batch_march(BatchPlan plan) {
+__global__ void __launch_bounds__(THREADS, p_min_blocks<THREADS, 16>()) k_batch_march(BatchPlan plan) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2* smem = reinterpret_cast<float2*>(smraw);
+    C2* smem = reinterpret_cast<C2*>(smraw);
     __shared__ int s_item_step, s_item_beam, s_item_tile, s_item_col, s_stop;
     __shared__ float2 s_rot;
     __shared__ long long s_k;
@@ -203,10 +210,10 @@ int ilog2i(int n) {
 template <int THREADS> int tiles_for(int log2n, bool col) {
     auto f = [&](auto nc) -> int {
         constexpr int N = decltype(nc)::value;
-        if constexpr (batch_supported<THREADS, N>()) return N / tile_lines<THREADS, N>();
+        if constexpr (batch_supported<THREADS, N>())
+            return col ? N / tile_cols<THREADS, N>() : N / 2 / tile_pairs<THREADS, N>();
         else return 0;
     };
-    (void)col;
     switch (log2n) {
         case 8: return f(std::integral_constant<int, 256>{});
         case 9: return f(std::integral_constant<int, 512>{});
@@ -233,8 +240,8 @@ BLayout blayout(int count, const nlse_params* ps) {
         L.field[b] = o; o = al256(o + (size_t)ps[b].n * ps[b].n * 8);
     }
     for (int b = 0; b < count; ++b) {
-        L.px[b] = o; o = al256(o + (size_t)kDither * ps[b].n * 8);
-        L.py[b] = o; o = al256(o + (size_t)kDither * ps[b].n * 8);
+        L.px[b] = o; o = al256(o + (size_t)kDitherP * ps[b].n * 8);
+        L.py[b] = o; o = al256(o + (size_t)kDitherP * py32_copy_bytes(ps[b].n));
     }
     int maxn = 0;
     for (int k = 0; k <= kBatchMaxLog2; ++k) L.tw[k] = 0;
@@ -242,7 +249,7 @@ BLayout blayout(int count, const nlse_params* ps) {
     for (int k = kBatchMinLog2; k <= kBatchMaxLog2; ++k) {
         bool used = false;
         for (int b = 0; b < count; ++b) used |= ps[b].n == (1 << k);
-        if (used) { L.tw[k] = o; o = al256(o + ((size_t)kDither * 8 << k)); }
+        if (used) { L.tw[k] = o; o = al256(o + (size_t)kDither * tw32_copy_bytes(1 << k)); }
     }
     L.beams = o;     o = al256(o + sizeof(BatchBeam) * count);
     L.col_off = o;   o = al256(o + sizeof(int) * (count + 1));
@@ -294,10 +301,10 @@ namespace {
 
 template <int THREADS> nlse_status plan_tiles(nlse_batch* B) {
     for (int b = 0; b < B->count; ++b) {
-        const int t = tiles_for<THREADS>(B->log2n[b], true);
-        if (t == 0) return NLSE_EUNSUPPORTED;
-        B->col_tiles[b] = t;
-        B->row_tiles[b] = t;
+        const int tc = tiles_for<THREADS>(B->log2n[b], true), tr = tiles_for<THREADS>(B->log2n[b], false);
+        if (tc == 0 || tr == 0) return NLSE_EUNSUPPORTED;
+        B->col_tiles[b] = tc;
+        B->row_tiles[b] = tr;
     }
     B->smem = batch_smem_max<THREADS>();
     return NLSE_OK;
@@ -408,17 +415,21 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     // a batched beam and the same beam alone use identical tables)
     std::vector<BatchBeam> desc(count);
     std::vector<int> coff(count + 1, 0), roff(count + 1, 0);
+    bool tw_done[kBatchMaxLog2 + 1] = {};
     for (int b = 0; b < count; ++b) {
         // the same table construction as a single grid, so that a batched beam
-        // and the same beam alone use identical tables
+        // and the same beam alone use identical tables; the twiddles depend on
+        // the size only and are uploaded once per size
+        const bool need_tw = !tw_done[B->log2n[b]];
+        tw_done[B->log2n[b]] = true;
         st = detail::upload_tables_f32(&params[b], B->stream, B->ws + lay.px[b], B->ws + lay.py[b],
-                                       B->ws + lay.tw[B->log2n[b]]);
+                                       need_tw ? B->ws + lay.tw[B->log2n[b]] : nullptr);
         if (st != NLSE_OK) { delete B; return st; }
         BatchBeam& d = desc[b];
-        d.field = reinterpret_cast<float2*>(B->ws + lay.field[b]);
+        d.field = reinterpret_cast<float4*>(B->ws + lay.field[b]);
         d.px = reinterpret_cast<const float2*>(B->ws + lay.px[b]);
-        d.py = reinterpret_cast<const float2*>(B->ws + lay.py[b]);
-        d.tw = reinterpret_cast<const float2*>(B->ws + lay.tw[B->log2n[b]]);
+        d.py = B->ws + lay.py[b];
+        d.tw = B->ws + lay.tw[B->log2n[b]];
         d.sc = detail::screen_coef_f32(&params[b]);
         d.log2n = B->log2n[b];
         d.col_tiles = B->col_tiles[b];

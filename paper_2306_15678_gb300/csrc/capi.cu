@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "../../include/nlse.h"
-#include "dispatch.cuh"
+#include "dispatch32.cuh"
 #include "hot_areas.cuh"
 #include "lens.cuh"
 #include "moments.cuh"
@@ -31,10 +31,19 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// bytes of one device table of n complex entries: FP32 tables hold kDither
-// dithered copies of 8-byte entries, FP64 tables one copy of 16-byte entries
-size_t table_bytes(int n, int precision) {
-    return precision == NLSE_FP64 ? (size_t)n * 16 : (size_t)kDither * n * 8;
+// bytes of the device propagator tables: FP64 one copy of n 16-byte entries
+// each; FP32 kDitherP dithered copies of P_x (n entries of 8 bytes) and of P_y
+// with the cross-lane factors (pass32.cuh: py32_copy_bytes)
+size_t px_bytes(int n, int precision) {
+    return precision == NLSE_FP64 ? (size_t)n * 16 : (size_t)kDitherP * n * 8;
+}
+size_t py_bytes(int n, int precision) {
+    return precision == NLSE_FP64 ? (size_t)n * 16 : (size_t)kDitherP * py32_copy_bytes(n);
+}
+// bytes of the twiddle region: FP64 one pass-major table of n 16-byte
+// entries; FP32 kDither twiddle blocks (pass32.cuh: tw32_copy_bytes)
+size_t tw_region_bytes(int n, int precision) {
+    return precision == NLSE_FP64 ? (size_t)n * 16 : (size_t)kDither * tw32_copy_bytes(n);
 }
 
 int log2_exact(int n) {
@@ -55,10 +64,9 @@ Layout layout_for(int n, int precision) {
     size_t o = 0;
     L.state = o;    o = align256(o + nn * cs);
     L.aux = o;      o = align256(o + nn * cs);
-    const size_t tb = table_bytes(n, precision);
-    L.tw = o;       o = align256(o + tb);
-    L.px = o;       o = align256(o + tb);
-    L.py = o;       o = align256(o + tb);
+    L.tw = o;       o = align256(o + tw_region_bytes(n, precision));
+    L.px = o;       o = align256(o + px_bytes(n, precision));
+    L.py = o;       o = align256(o + py_bytes(n, precision));
     L.partials = o; o = align256(o + (size_t)n * 2 * sizeof(double));
     L.diag = o;     o = align256(o + (size_t)kDiagBatch * n * 2 * sizeof(double));
     L.hist = o;     o = align256(o + (size_t)kHistCap * 2 * sizeof(double));
@@ -98,16 +106,20 @@ inline double signed_bin(int m, int n) { return (double)(m < n / 2 ? m : m - n);
 // Separable diffraction tables (Eq. 1-2, Lap_perp -> -(kx^2 + ky^2)):
 // P_x(m) = exp(i k_m^2 dz / (2 k0)), P_y(m) = the same divided by n^2 (the
 // normalisation of the inverse 2D transform).  Phases in FP64, reduced mod 2 pi.
+// phase k_m^2 dz / (2 k0) of FFT bin m, reduced mod 2 pi (0 without diffraction)
+double propagator_phase(const nlse_params* p, int m) {
+    const double k0 = kTwoPi * p->n0 / p->lambda0;
+    const double k = kTwoPi * signed_bin(m, p->n) / p->L;
+    return (p->terms & NLSE_DIFFRACTION) ? std::fmod(k * k * p->dz / (2.0 * k0), kTwoPi) : 0.0;
+}
+
 void propagator_tables(const nlse_params* p, std::vector<double>& px, std::vector<double>& py) {
     const int n = p->n;
-    const double k0 = kTwoPi * p->n0 / p->lambda0;
     const double inv_n2 = 1.0 / ((double)n * (double)n);
-    const bool diffr = (p->terms & NLSE_DIFFRACTION) != 0;
     px.resize(2 * (size_t)n);
     py.resize(2 * (size_t)n);
     for (int m = 0; m < n; ++m) {
-        const double k = kTwoPi * signed_bin(m, n) / p->L;
-        double ph = diffr ? std::fmod(k * k * p->dz / (2.0 * k0), kTwoPi) : 0.0;
+        const double ph = propagator_phase(p, m);
         const double c = std::cos(ph), s = std::sin(ph);
         px[2 * m] = c;
         px[2 * m + 1] = s;
@@ -175,6 +187,7 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     c.K = p->K;
     c.active = (p->terms & (NLSE_KERR | NLSE_PLASMA | NLSE_MPA)) ? 1 : 0;
     c.has_gain = (c.re_k != (T)0 || c.re_p != (T)0 || c.re_a != (T)0) ? 1 : 0;
+    c.real_gains = (c.re_k == (T)0 && c.re_p == (T)0 && c.im_a == (T)0) ? 1 : 0;
     c.reps = 1;
     c.scale = (T)1;
     c.exact = (p->scheme & NLSE_EXACT_SCREEN) ? 1 : 0;
@@ -182,62 +195,167 @@ template <typename T> ScreenCoef<T> screen_coef(const nlse_params* p) {
     return c;
 }
 
-// Dithered rounding (see fft.cuh): the FP32 neighbour of w below or above it,
-// the one above when the fraction of an FP32 unit by which w exceeds the
-// lower neighbour is greater than the threshold u in (0, 1).
-float dround(double w, double u) {
-    float lo = (float)w;
-    if ((double)lo > w) lo = std::nextafter(lo, -INFINITY);
-    if ((double)lo == w) return lo;
-    const float hi = std::nextafter(lo, INFINITY);
-    const double frac = (w - (double)lo) / ((double)hi - (double)lo);
-    return frac > u ? hi : lo;
+// Dithered rounding (fft.cuh, pass32.cuh): copy d of an FP32 table holds, for
+// each component w of each entry, the FP32 neighbour of w above it when the
+// fraction of an FP32 unit by which w exceeds its lower neighbour is above the
+// copy's threshold, else the one below.  dsplit gives the two neighbours
+// lo <= w <= hi and that fraction (0 when w is an FP32 value).
+struct DSplit {
+    float lo, hi;
+    double frac;
+};
+DSplit dsplit(double w) {
+    DSplit r;
+    r.lo = (float)w;
+    if ((double)r.lo > w) r.lo = std::nextafter(r.lo, -INFINITY);
+    if ((double)r.lo == w) { r.hi = r.lo; r.frac = 0.0; return r; }
+    r.hi = std::nextafter(r.lo, INFINITY);
+    r.frac = (w - (double)r.lo) / ((double)r.hi - (double)r.lo);
+    return r;
 }
-// fixed pseudo-random offset in [0, kDither) of (table, entry, component)
-int dither_offset(uint64_t table_id, uint64_t entry, int comp) {
+// fixed pseudo-random offset in [0, copies) of (table, entry, component)
+int dither_offset(uint64_t table_id, uint64_t entry, int comp, int copies = kDither) {
     uint64_t z = table_id * 0x9E3779B97F4A7C15ull + entry * 2 + (uint64_t)comp + 0x632BE59BD9B4E019ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    return (int)(z % (uint64_t)kDither);
+    return (int)(z % (uint64_t)copies);
 }
 // identifiers of the dithered tables (distinct offsets per table)
-enum : uint64_t { kTabTwiddle = 1, kTabPx = 2, kTabPy = 3 };
+enum : uint64_t {
+    kTabTwiddle = 1, kTabPx = 2, kTabPy = 3, kTabRowPair = 4, kTabColPair = 5, kTabCross = 6, kTabRowPair8 = 7,
+    kTabColPair8 = 8
+};
 
-// FP64 complex table (re, im pairs) -> device entries: the FP64 values, or
-// kDither FP32 copies, copy d rounding entry e's component c with threshold
-// ((d + o) mod kDither + 1/2) / kDither, o = dither_offset(table, e, c)
-template <typename T> void round_table(const std::vector<double>& in, uint64_t table_id, std::vector<T>& out);
-template <>
-void round_table<double>(const std::vector<double>& in, uint64_t, std::vector<double>& out) {
-    out = in;
-}
-template <>
-void round_table<float>(const std::vector<double>& in, uint64_t table_id, std::vector<float>& out) {
-    const size_t n = in.size() / 2;
-    out.resize((size_t)kDither * 2 * n);
-    for (size_t e = 0; e < n; ++e)
-        for (int c = 0; c < 2; ++c) {
-            const int o = dither_offset(table_id, e, c);
-            for (int d = 0; d < kDither; ++d)
-                out[(size_t)d * 2 * n + 2 * e + c] = dround(in[2 * e + c], ((d + o) % kDither + 0.5) / kDither);
-        }
+// Threshold of copy d (of `copies`, a power of two) for an entry with offset
+// o: the copies take the thresholds (q + 1/2) / copies in bit-reversed order
+// of q = (d + o) mod copies, so that a run of consecutive steps rounds up and
+// down in alternation (every partial sum of the rounding errors over a cycle
+// stays within about one unit) instead of rounding the same way for half a
+// cycle; over a whole cycle every threshold is used once, as before.
+double dither_u(int d, int o, int copies = kDither) {
+    const int q = (d + o) % copies;
+    int r = 0;
+    for (int b = 1, c = copies >> 1; b < copies; b <<= 1, c >>= 1)
+        if (q & b) r |= c;
+    return (r + 0.5) / copies;
 }
 
-// Twiddle table of step k (0-based count of the steps taken before it): copy
-// k mod kDither in FP32, the table itself in FP64.
+
+// Twiddles of step k (0-based count of the steps taken before it): the start
+// of twiddle block k mod kDither in FP32, the table itself in FP64.
 template <typename T> const typename tab_of<T>::type* twiddles_at(const unsigned char* table, int n, int64_t k) {
-    const auto* t = reinterpret_cast<const typename tab_of<T>::type*>(table);
-    return sizeof(T) == 4 ? t + (size_t)(k & (kDither - 1)) * n : t;
+    if (sizeof(T) == 4) table += (size_t)(k & (kDither - 1)) * tw32_copy_bytes(n);
+    return reinterpret_cast<const typename tab_of<T>::type*>(table);
 }
 // twiddles of the one-off transforms (load prologue, readouts): copy 0
 template <typename T> const typename tab_of<T>::type* twiddles_fixed(const unsigned char* table) {
     return reinterpret_cast<const typename tab_of<T>::type*>(table);
 }
-// copy of a propagator table for step k
-template <typename T> const typename tab_of<T>::type* table_at(const unsigned char* table, int n, int64_t k) {
-    const auto* t = reinterpret_cast<const typename tab_of<T>::type*>(table);
-    return sizeof(T) == 4 ? t + (size_t)(k & (kDither - 1)) * n : t;
+// copies of the propagator tables for step k
+template <typename T> const typename tab_of<T>::type* px_at(const unsigned char* table, int n, int64_t k) {
+    if (sizeof(T) == 4) table += (size_t)(k & (kDitherP - 1)) * n * 8;
+    return reinterpret_cast<const typename tab_of<T>::type*>(table);
+}
+template <typename T> const typename tab_of<T>::type* py_at(const unsigned char* table, int n, int64_t k) {
+    if (sizeof(T) == 4) table += (size_t)(k & (kDitherP - 1)) * py32_copy_bytes(n);
+    return reinterpret_cast<const typename tab_of<T>::type*>(table);
+}
+
+void put_twiddle(std::vector<double>& out, size_t idx, long long m, long long period) {
+    const double a = kTwoPi * (double)(m % period) / (double)period;
+    out[2 * idx] = std::cos(a);
+    out[2 * idx + 1] = -std::sin(a);
+}
+// FP64 pair table of an l-point transform of the pair engine (pair.cuh) with
+// elements per thread e_max (16 or 8, at most l): per pass of stride ns > 1 and
+// radix r = r1 r2, the entries W_{r1 ns}^{rA k} then W_{r ns}^{i kB}; angles
+// reduced exactly in integers.
+void pair_table(int l, int e_max, std::vector<double>& out) {
+    const int e = std::min(e_max, l);
+    out.assign(2 * (size_t)pr::pair_tab_entries(l, e), 0.0);
+    size_t off = 0;
+    for (int cur = 1; cur < l;) {
+        const int r = std::min(e, l / cur);
+        if (cur > 1) {
+            const int r1 = pr::split1(r), r2 = pr::split2(r);
+            for (int ra = 1; ra < r1; ++ra)
+                for (int k = 0; k < cur; ++k) put_twiddle(out, off + (size_t)(ra - 1) * cur + k, (long long)ra * k, (long long)r1 * cur);
+            off += (size_t)(r1 - 1) * cur;
+            for (int i = 1; i < r2; ++i)
+                for (int kb = 0; kb < r1 * cur; ++kb)
+                    put_twiddle(out, off + (size_t)(i - 1) * r1 * cur + kb, (long long)i * kb, (long long)r * cur);
+            off += (size_t)(r2 - 1) * r1 * cur;
+        }
+        cur *= r;
+    }
+}
+
+// FP32 tables of one grid: kDither twiddle blocks (single-line table, row and
+// column pair tables), P_x (kDitherP x n entries) and P_y with the cross-lane
+// factors W_n^k (kDitherP x (n/2 pair entries (k, k + n/2), n/2 entries));
+// every component of every entry dithered independently.  The cross-lane and propagator factors e^{i phi} are
+// stored as (cos phi - 1, sin phi) (pass32.cuh), cos phi - 1 = -2 sin^2(phi/2)
+// in FP64; P_y without its 1/n^2, which the kernel applies with P_x.
+struct HostTables32 {
+    std::vector<unsigned char> tw;
+    std::vector<float> px, py;
+};
+void build_tables_f32(const nlse_params* p, HostTables32& t) {
+    const int n = p->n, h = n / 2;
+    std::vector<double> dp(2 * (size_t)n), single, cross(2 * (size_t)h);
+    std::vector<double> pt[4];  // row E 16, row E 8, column E 16, column E 8
+    for (int m = 0; m < n; ++m) {  // (cos phi - 1, sin phi) of P_x = P_y n^2
+        const double ph = propagator_phase(p, m), sh = std::sin(0.5 * ph);
+        dp[2 * m] = -2.0 * sh * sh;
+        dp[2 * m + 1] = std::sin(ph);
+    }
+    twiddle_table(n, std::min(n, 16), single);
+    pair_table(n, 16, pt[0]);
+    pair_table(n, 8, pt[1]);
+    pair_table(h, 16, pt[2]);
+    pair_table(h, 8, pt[3]);
+    for (int k = 0; k < h; ++k) {  // W_n^k = exp(-2 pi i k / n) as (cos - 1, sin)
+        const double a = kTwoPi * (double)k / (double)n, sh = std::sin(0.5 * a);
+        cross[2 * k] = -2.0 * sh * sh;
+        cross[2 * k + 1] = -std::sin(a);
+    }
+    // the kDitherP thresholds in copy order for offset 0 (offset o: index d + o)
+    std::vector<double> uq(2 * (size_t)kDitherP);
+    for (int q = 0; q < 2 * kDitherP; ++q) uq[q] = dither_u(q % kDitherP, 0, kDitherP);
+    auto dither_into = [&](double w, uint64_t table, uint64_t e, int c, float* dst, size_t stride) {
+        const DSplit sp = dsplit(w);
+        const int o = dither_offset(table, e, c, kDitherP);
+        for (int d = 0; d < kDitherP; ++d) dst[(size_t)d * stride] = sp.frac > uq[d + o] ? sp.hi : sp.lo;
+    };
+    // P_x: kDitherP copies of n entries
+    t.px.assign((size_t)kDitherP * 2 * n, 0.0f);
+    for (int e = 0; e < n; ++e)
+        for (int c = 0; c < 2; ++c) dither_into(dp[2 * e + c], kTabPx, e, c, t.px.data() + 2 * e + c, 2 * (size_t)n);
+    // P_y pair entries and the cross-lane factors: kDitherP copies
+    const size_t pyf = py32_copy_bytes(n) / 4;  // floats per copy
+    t.py.assign((size_t)kDitherP * pyf, 0.0f);
+    for (int k = 0; k < h; ++k)
+        for (int c = 0; c < 2; ++c) {  // c = 0: cos - 1, 1: sin; lanes k and k + h
+            dither_into(dp[2 * k + c], kTabPy, k, c, t.py.data() + 4 * k + 2 * c, pyf);
+            dither_into(dp[2 * (k + h) + c], kTabPy, k + h, c, t.py.data() + 4 * k + 2 * c + 1, pyf);
+            dither_into(cross[2 * k + c], kTabCross, k, c, t.py.data() + 4 * h + 2 * k + c, pyf);
+        }
+    // twiddle blocks: kDither copies (stride cb bytes)
+    const size_t cb = tw32_copy_bytes(n), cbf = cb / 4;
+    t.tw.assign((size_t)kDither * cb, 0);
+    float* tw = reinterpret_cast<float*>(t.tw.data());
+    for (size_t e = 0; e < single.size() / 2; ++e)
+        for (int c = 0; c < 2; ++c) dither_into(single[2 * e + c], kTabTwiddle, e, c, tw + 2 * e + c, cbf);
+    const uint64_t pid[4] = {kTabRowPair, kTabRowPair8, kTabColPair, kTabColPair8};
+    const size_t poff[4] = {tw32_row_off(n, 16), tw32_row_off(n, 8), tw32_col_off(n, 16), tw32_col_off(n, 8)};
+    for (int q = 0; q < 4; ++q)
+        for (size_t e = 0; e < pt[q].size() / 2; ++e)
+            for (int c = 0; c < 2; ++c) {  // (wx, wx, wy, wy)
+                float* f = tw + poff[q] / 4 + 4 * e + 2 * c;
+                dither_into(pt[q][2 * e + c], pid[q], e, c, f, cbf);
+                for (int d = 0; d < kDither; ++d) f[(size_t)d * cbf + 1] = f[(size_t)d * cbf];
+            }
 }
 
 }  // namespace
@@ -254,6 +372,7 @@ struct nlse_grid {
     int diag_pending;    // diagnostic steps recorded in the diag buffer, not yet finalised
     int loaded;
     int cols;  // column tile of the column pass
+    int row_radix;  // radix of the row pass (FP32: 16 or 8)
     unsigned debug_extra_tx;  // test hook of the staged column pass (NLSE_DEBUG_COL_EXTRA_TX), 0 in use
     double theta;  // accumulated global phase of the stored field, mod 2 pi
     const KernelSet<float>* k32;
@@ -340,12 +459,16 @@ template <typename T> VT<T> unrot_value(double theta) {
 }
 inline double* dat(nlse_grid* g, size_t off) { return reinterpret_cast<double*>(g->ws + off); }
 
+// per-block partials of a row pass of radix rad
+template <typename T> int row_parts(const KernelSet<T>* ks, int rad) { return rad == 8 ? ks->row_blocks8 : ks->row_blocks; }
+
 // Finalise the pending diagnostic steps into the history ring (one block per step).
 template <typename T> nlse_status flush_diag(nlse_grid* g) {
     if (g->diag_pending == 0) return NLSE_OK;
     const double dx = g->p.L / g->p.n;
     k_finalize_batch<<<g->diag_pending, 256, 0, g->stream>>>(
-        dat(g, g->lay.diag), Sel<T>::ks(g)->row_blocks, dx * dx, dat(g, g->lay.hist), (long long)g->hist_count,
+        dat(g, g->lay.diag), row_parts(Sel<T>::ks(g), g->row_radix), dx * dx, dat(g, g->lay.hist),
+        (long long)g->hist_count,
         kHistCap, reinterpret_cast<int*>(g->ws + g->lay.status));
     if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
     g->hist_count += g->diag_pending;
@@ -377,13 +500,13 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
             sc.reps = 1;
             sc.scale = (T)1 / (T)n;
             if (ks->row_pass(field, field, twiddles_at<T>(g->ws + g->lay.tw, n, k), sc, partials, false,
-                             g->stream) != cudaSuccess)
+                             g->row_radix, g->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             sc.scale = (T)1;
         }
         const WT<T>* tw = twiddles_at<T>(g->ws + g->lay.tw, n, k);
-        const WT<T>* px = table_at<T>(g->ws + g->lay.px, n, k);
-        const WT<T>* py = table_at<T>(g->ws + g->lay.py, n, k);
+        const WT<T>* px = px_at<T>(g->ws + g->lay.px, n, k);
+        const WT<T>* py = py_at<T>(g->ws + g->lay.py, n, k);
         double th = 0.0;
         const WT<T> rot = rot_for_step<T>(k, &th);
         cudaError_t e = ks->col_pass(field, field, tw, px, py, rot, g->cols,
@@ -394,9 +517,9 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
         const bool diag = g->p.diag_every > 0 && ((g->steps + 1) % g->p.diag_every) == 0;
         // a diagnostic step leaves its per-block partials in the next slot of the
         // diag buffer; a full buffer is finalised into the history in one launch
-        double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * ks->row_blocks;
+        double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * row_parts(ks, g->row_radix);
         sc.reps = strang && s + 1 < nsteps ? 2 : 1;
-        e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->stream);
+        e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->row_radix, g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (diag && ++g->diag_pending == kDiagBatch && flush_diag<T>(g) != NLSE_OK) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -434,26 +557,31 @@ nlse_status fetch_readout(nlse_grid* g, double out[2]) {
     return NLSE_OK;
 }
 
-template <typename T> nlse_status upload_tables(nlse_grid* g) {
+template <typename T> nlse_status upload_tables(nlse_grid* g);
+template <> nlse_status upload_tables<double>(nlse_grid* g) {
     std::vector<double> px, py, tw;
     propagator_tables(&g->p, px, py);
-    // elements per thread of the kernels: 16 in FP32, 8 in FP64 (at most n)
-    const int ept = std::min(g->p.n, sizeof(T) == 4 ? 16 : 8);
-    twiddle_table(g->p.n, ept, tw);
-    std::vector<T> a, b, c;
-    round_table(px, kTabPx, a);
-    round_table(py, kTabPy, b);
-    round_table(tw, kTabTwiddle, c);
-    const size_t bytes = a.size() * sizeof(T);
-    const size_t tw_bytes = c.size() * sizeof(T);
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(g->ws + g->lay.px, a.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
-        return NLSE_ECUDA;
-    if ((e = cudaMemcpyAsync(g->ws + g->lay.py, b.data(), bytes, cudaMemcpyHostToDevice, g->stream)))
-        return NLSE_ECUDA;
-    if ((e = cudaMemcpyAsync(g->ws + g->lay.tw, c.data(), tw_bytes, cudaMemcpyHostToDevice, g->stream)))
+    // elements per thread of the FP64 kernels: 8 (at most n)
+    twiddle_table(g->p.n, std::min(g->p.n, 8), tw);
+    const size_t bytes = px.size() * sizeof(double);
+    if (cudaMemcpyAsync(g->ws + g->lay.px, px.data(), bytes, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->ws + g->lay.py, py.data(), bytes, cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->ws + g->lay.tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        g->stream) != cudaSuccess)
         return NLSE_ECUDA;
     // the host vectors die at return: make the copies complete first
+    return cuerr(cudaStreamSynchronize(g->stream));
+}
+template <> nlse_status upload_tables<float>(nlse_grid* g) {
+    HostTables32 t;
+    build_tables_f32(&g->p, t);
+    if (cudaMemcpyAsync(g->ws + g->lay.px, t.px.data(), t.px.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->ws + g->lay.py, t.py.data(), t.py.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g->ws + g->lay.tw, t.tw.data(), t.tw.size(), cudaMemcpyHostToDevice, g->stream) !=
+            cudaSuccess)
+        return NLSE_ECUDA;
     return cuerr(cudaStreamSynchronize(g->stream));
 }
 
@@ -464,20 +592,13 @@ namespace detail {
 
 nlse_status upload_tables_f32(const nlse_params* p, cudaStream_t s, unsigned char* px, unsigned char* py,
                               unsigned char* tw) {
-    std::vector<double> dpx, dpy, dtw;
-    propagator_tables(p, dpx, dpy);
-    std::vector<float> a, b, c;
-    round_table(dpx, kTabPx, a);
-    round_table(dpy, kTabPy, b);
-    if (cudaMemcpyAsync(px, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(py, b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    HostTables32 t;
+    build_tables_f32(p, t);
+    if (cudaMemcpyAsync(px, t.px.data(), t.px.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(py, t.py.data(), t.py.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return NLSE_ECUDA;
-    if (tw) {
-        twiddle_table(p->n, std::min(p->n, 16), dtw);
-        round_table(dtw, kTabTwiddle, c);
-        if (cudaMemcpyAsync(tw, c.data(), c.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return NLSE_ECUDA;
-    }
+    if (tw && cudaMemcpyAsync(tw, t.tw.data(), t.tw.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return NLSE_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
 }
 
@@ -682,10 +803,12 @@ nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_works
     if (p->precision == NLSE_FP64) {
         g->k64 = kernels_f64(k);
         g->cols = g->k64->col_default;
+        g->row_radix = g->k64->row_radix_default;
         g->sc64 = screen_coef<double>(&screen_p);
     } else {
         g->k32 = kernels_f32(k);
         g->cols = g->k32->col_default;
+        g->row_radix = g->k32->row_radix_default;
         g->sc32 = screen_coef<float>(&screen_p);
     }
     if (const char* env = std::getenv("NLSE_DEBUG_COL_EXTRA_TX")) g->debug_extra_tx = (unsigned)std::atoi(env);
@@ -780,6 +903,17 @@ nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols) {
             return NLSE_OK;
         }
     return NLSE_EUNSUPPORTED;
+}
+
+nlse_status nlse_set_row_radix(nlse_grid* g, int32_t radix) {
+    if (!g) return NLSE_EINVAL;
+    const int mask = g->p.precision == NLSE_FP64 ? g->k64->row_radix_mask : g->k32->row_radix_mask;
+    const int bit = radix == 16 ? 1 : radix == 8 ? 2 : 0;
+    if (!(mask & bit)) return NLSE_EUNSUPPORTED;
+    // recorded partials carry the block count of the radix they were made with
+    if (flush_diag_any(g) != NLSE_OK) return NLSE_ECUDA;
+    g->row_radix = radix;
+    return NLSE_OK;
 }
 
 nlse_status nlse_steps_taken(nlse_grid* g, int64_t* steps) {
@@ -1078,12 +1212,11 @@ AdjLayout adj_layout_for(int n, int precision, int nsteps, int ckpt) {
     size_t o = 0;
     L.state = o;    o = align256(o + field);
     L.gam = o;      o = align256(o + field);
-    const size_t tb = table_bytes(n, precision);
-    L.tw = o;       o = align256(o + tb);
-    L.px = o;       o = align256(o + tb);
-    L.py = o;       o = align256(o + tb);
-    L.pxc = o;      o = align256(o + tb);
-    L.pyc = o;      o = align256(o + tb);
+    L.tw = o;       o = align256(o + tw_region_bytes(n, precision));
+    L.px = o;       o = align256(o + px_bytes(n, precision));
+    L.py = o;       o = align256(o + py_bytes(n, precision));
+    L.pxc = o;      o = align256(o + px_bytes(n, precision));
+    L.pyc = o;      o = align256(o + py_bytes(n, precision));
     L.seg = o;      o = align256(o + field * (size_t)ckpt);
     L.ckpt = o;     o = align256(o + field * (size_t)L.nck);
     L.target = o;   o = align256(o + (size_t)n * n * sizeof(double));
@@ -1115,6 +1248,7 @@ struct nlse_adjoint {
     unsigned char* ws;
     AdjLayout lay;
     int cols;
+    int row_radix;
     const KernelSet<float>* k32;
     const KernelSet<double>* k64;
     AdjCoef<float> ac32;
@@ -1143,29 +1277,45 @@ inline size_t adj_field_bytes(const nlse_adjoint* a) {
     return (size_t)a->p.n * a->p.n * (a->p.precision == NLSE_FP64 ? 16 : 8);
 }
 
-template <typename T> nlse_status adj_upload(nlse_adjoint* a) {
+template <typename T> nlse_status adj_upload(nlse_adjoint* a);
+template <> nlse_status adj_upload<double>(nlse_adjoint* a) {
     std::vector<double> px, py, tw;
     propagator_tables(&a->p, px, py);
-    const int ept = std::min(a->p.n, sizeof(T) == 4 ? 16 : 8);
-    twiddle_table(a->p.n, ept, tw);
-    const std::vector<double>* src[3] = {&tw, &px, &py};
-    const uint64_t ids[3] = {kTabTwiddle, kTabPx, kTabPy};
+    twiddle_table(a->p.n, std::min(a->p.n, 8), tw);
+    // conjugated propagator tables: the conjugates of the same values
+    std::vector<double> pxc = px, pyc = py;
+    for (size_t i = 1; i < pxc.size(); i += 2) { pxc[i] = -pxc[i]; pyc[i] = -pyc[i]; }
+    const std::vector<double>* src[5] = {&tw, &px, &py, &pxc, &pyc};
     const size_t off[5] = {a->lay.tw, a->lay.px, a->lay.py, a->lay.pxc, a->lay.pyc};
-    std::vector<T> rounded[5];
-    for (int t = 0; t < 3; ++t) round_table(*src[t], ids[t], rounded[t]);
-    // conjugated propagator tables: the conjugates of the same rounded values
-    for (int t = 3; t < 5; ++t) {
-        rounded[t] = rounded[t - 2];
-        for (size_t i = 1; i < rounded[t].size(); i += 2) rounded[t][i] = -rounded[t][i];
-    }
-    for (int t = 0; t < 5; ++t) {
-        const std::vector<T>& r = rounded[t];
-        if (cudaMemcpyAsync(a->ws + off[t], r.data(), r.size() * sizeof(T), cudaMemcpyHostToDevice,
+    for (int t = 0; t < 5; ++t)
+        if (cudaMemcpyAsync(a->ws + off[t], src[t]->data(), src[t]->size() * sizeof(double), cudaMemcpyHostToDevice,
                             a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
-    }
-    return NLSE_OK;
+    return cudaStreamSynchronize(a->stream) == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
+}
+template <> nlse_status adj_upload<float>(nlse_adjoint* a) {
+    HostTables32 t;
+    build_tables_f32(&a->p, t);
+    // conjugated propagator tables: the conjugates of the same rounded values
+    // (P_x entries (d, s); P_y entries (d, d', s, s'))
+    std::vector<float> pxc = t.px, pyc = t.py;
+    for (size_t i = 1; i < pxc.size(); i += 2) pxc[i] = -pxc[i];
+    // in every copy the n/2 P_y entries (d, d', s, s') are conjugated; the
+    // cross-lane factors that follow belong to the transform and stay as they are
+    const int hn = a->p.n / 2;
+    const size_t pyf = py32_copy_bytes(a->p.n) / 4;
+    for (size_t c0 = 0; c0 < pyc.size(); c0 += pyf)
+        for (int k = 0; k < hn; ++k) {
+            pyc[c0 + 4 * k + 2] = -pyc[c0 + 4 * k + 2];
+            pyc[c0 + 4 * k + 3] = -pyc[c0 + 4 * k + 3];
+        }
+    const void* src[5] = {t.tw.data(), t.px.data(), t.py.data(), pxc.data(), pyc.data()};
+    const size_t bytes[5] = {t.tw.size(), t.px.size() * 4, t.py.size() * 4, pxc.size() * 4, pyc.size() * 4};
+    const size_t off[5] = {a->lay.tw, a->lay.px, a->lay.py, a->lay.pxc, a->lay.pyc};
+    for (int q = 0; q < 5; ++q)
+        if (cudaMemcpyAsync(a->ws + off[q], src[q], bytes[q], cudaMemcpyHostToDevice, a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
+    return cudaStreamSynchronize(a->stream) == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
 }
 
 template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* src, int on_device, double* loss) {
@@ -1191,17 +1341,18 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
                             cudaMemcpyDeviceToDevice, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
         const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
-        if (ks->col_pass(state, state, tws, table_at<T>(a->ws + a->lay.px, n, s),
-                         table_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols, nullptr,
+        if (ks->col_pass(state, state, tws, px_at<T>(a->ws + a->lay.px, n, s),
+                         py_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols, nullptr,
                          0u, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (ks->row_pass(state, state, tws, sc, partials, false, a->stream) != cudaSuccess) return NLSE_ECUDA;
+        if (ks->row_pass(state, state, tws, sc, partials, false, a->row_radix, a->stream) != cudaSuccess)
+            return NLSE_ECUDA;
     }
     double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
     if (ks->loss_seed(state, aat<T>(a, a->lay.gam), reinterpret_cast<const double*>(a->ws + a->lay.target),
                       tw, 1.0 / a->sum_d2, partials, a->stream) != cudaSuccess)
         return NLSE_ECUDA;
-    k_finalize<<<1, 256, 0, a->stream>>>(partials, ks->row_blocks, 1.0 / a->sum_d2, result,
+    k_finalize<<<1, 256, 0, a->stream>>>(partials, ks->adj_blocks, 1.0 / a->sum_d2, result,
                                          reinterpret_cast<int*>(result + 4));
     if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
     double r[2];
@@ -1232,19 +1383,20 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
             return NLSE_ECUDA;
         for (int s = c0; s < c1; ++s) {  // recompute the segment, keeping T_s
             const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
-            if (ks->col_pass(state, seg(s - c0), tws, table_at<T>(a->ws + a->lay.px, n, s),
-                             table_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols,
+            if (ks->col_pass(state, seg(s - c0), tws, px_at<T>(a->ws + a->lay.px, n, s),
+                             py_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols,
                              nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             if (s + 1 < c1 &&
-                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->stream) != cudaSuccess)
+                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->row_radix, a->stream) !=
+                    cudaSuccess)
                 return NLSE_ECUDA;
         }
         for (int s = c1 - 1; s >= c0; --s) {  // reverse the segment with the forward step's constants
             const WT<T>* tws = twiddles_at<T>(a->ws + a->lay.tw, n, s);
             if (ks->adj_row(gam, seg(s - c0), tws, ac, acc, a->stream) != cudaSuccess) return NLSE_ECUDA;
-            if (ks->col_pass(gam, gam, tws, table_at<T>(a->ws + a->lay.pxc, n, s),
-                             table_at<T>(a->ws + a->lay.pyc, n, s), conj_of(rot_for_step<T>(s, nullptr)), a->cols,
+            if (ks->col_pass(gam, gam, tws, px_at<T>(a->ws + a->lay.pxc, n, s),
+                             py_at<T>(a->ws + a->lay.pyc, n, s), conj_of(rot_for_step<T>(s, nullptr)), a->cols,
                              nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
         }
@@ -1264,7 +1416,7 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
         return NLSE_ECUDA;
     if (cudaStreamSynchronize(a->stream) != cudaSuccess) return NLSE_ECUDA;
     for (int q = 0; q < 6; ++q) dtheta[q] = 0.0;
-    for (int b = 0; b < ks->row_blocks; ++b)  // fixed order: deterministic
+    for (int b = 0; b < ks->adj_blocks; ++b)  // fixed order: deterministic
         for (int q = 0; q < 6; ++q) dtheta[q] += h[6 * (size_t)b + q];
     return NLSE_OK;
 }
@@ -1306,11 +1458,13 @@ nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ck
     if (p->precision == NLSE_FP64) {
         a->k64 = kernels_f64(k);
         a->cols = a->k64->col_default;
+        a->row_radix = a->k64->row_radix_default;
         a->ac64 = adj_coef<double>(p);
         st = adj_upload<double>(a);
     } else {
         a->k32 = kernels_f32(k);
         a->cols = a->k32->col_default;
+        a->row_radix = a->k32->row_radix_default;
         a->ac32 = adj_coef<float>(p);
         st = adj_upload<float>(a);
     }

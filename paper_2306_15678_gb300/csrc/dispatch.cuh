@@ -15,21 +15,31 @@ namespace nlse {
 
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per block (sm_100/103)
 // column-tile codes: a width of 1..16 columns per block, or'ed with kColTma
-// for the variant that stages the tile with bulk tensor copies (tma.cuh)
+// for the variant that stages the tile with bulk tensor copies (tma.cuh), and
+// in FP32 with kColR8 for the radix-8 column transform (8 elements per thread;
+// radix 16 without it)
 constexpr int kColTma = 0x100;
-constexpr int kColOptionCount = 10;
-constexpr int kColOptions[kColOptionCount] = {1, 2, 4, 8, 16,
-                                              kColTma | 1, kColTma | 2, kColTma | 4, kColTma | 8, kColTma | 16};
+constexpr int kColR8 = 0x200;
+constexpr int kColOptionCount = 20;
+constexpr int kColOptions[kColOptionCount] = {
+    1, 2, 4, 8, 16, kColTma | 1, kColTma | 2, kColTma | 4, kColTma | 8, kColTma | 16,
+    kColR8 | 1, kColR8 | 2, kColR8 | 4, kColR8 | 8, kColR8 | 16,
+    kColR8 | kColTma | 1, kColR8 | kColTma | 2, kColR8 | kColTma | 4, kColR8 | kColTma | 8, kColR8 | kColTma | 16};
 
 template <typename T> struct KernelSet {
     using V = typename vec2<T>::type;
     using W = typename tab_of<T>::type;
     int n;
-    int row_blocks;    // blocks of the row-oriented kernels (n / rows_per_block)
+    int row_blocks;    // blocks (partials) of the readout and of the default-radix row pass
+    int row_blocks8;   // blocks (partials) of the radix-8 row pass
+    int adj_blocks;    // blocks (partials) of the loss seed and the backward row pass
     int col_mask;      // bit i set: column tile kColOptions[i] is instantiated
     int col_default;   // default column tile
+    int row_radix_mask;     // bit 0: radix 16 available for the row pass, bit 1: radix 8
+    int row_radix_default;  // default radix of the row pass (16 or 8)
+    // rad: radix of the row transform (16 or 8; FP64: 8)
     cudaError_t (*row_pass)(const V* src, V* dst, const W* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, cudaStream_t s);
+                            bool diag, int rad, cudaStream_t s);
     // status: device status word (bit 1: a bounded wait ran out), may be null;
     // extra_tx: test hook of the staged variant (0 in use)
     cudaError_t (*col_pass)(const V* src, V* dst, const W* tw, const W* px, const W* py, W rot,
@@ -57,6 +67,35 @@ template <auto Kernel> inline cudaError_t ensure_smem(int bytes) {
     e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done |= bit;
     return e;
+}
+
+// The same, and the preferred shared-memory carveout of the kernel set to the
+// smallest share of the SM's unified L1/shared array that holds `blocks`
+// resident blocks of `bytes` dynamic shared memory each: the rest stays L1
+// cache, where the twiddle and propagator tables are read from.
+template <auto Kernel> inline cudaError_t ensure_smem_carveout(int bytes, int blocks) {
+    static unsigned long long done = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    if (bytes > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, Kernel)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    // 1 KB per block is reserved by the system
+    const long long need = (long long)blocks * ((long long)bytes + (long long)fa.sharedSizeBytes + 1024);
+    int pct = per_sm > 0 ? (int)((need * 100 + per_sm - 1) / per_sm) : 100;
+    pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+    if ((e = cudaFuncSetAttribute(Kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess)
+        return e;
+    done |= bit;
+    return cudaSuccess;
 }
 
 template <typename T, int N> constexpr int row_smem_bytes() {
@@ -89,7 +128,7 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, int smem, cu
 template <typename T, int N>
 cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
                             const typename tab_of<T>::type* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, cudaStream_t s) {
+                            bool diag, int, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
     cudaError_t e;
@@ -296,8 +335,12 @@ template <typename T, int N> KernelSet<T> make_set() {
     KernelSet<T> k;
     k.n = N;
     k.row_blocks = N / rows_per_block<T, N>();
+    k.row_blocks8 = k.row_blocks;
+    k.adj_blocks = k.row_blocks;
     k.col_mask = col_mask<T, N>();
     k.col_default = col_default<T, N>();
+    k.row_radix_mask = 2;  // the single-line engine of fft.cuh: radix 8 in FP64
+    k.row_radix_default = 8;
     k.row_pass = &launch_row_pass<T, N>;
     k.col_pass = &launch_col_pass<T, N>;
     k.row_forward = &launch_row_forward<T, N>;

@@ -30,10 +30,13 @@
 // Instead each table exists in kDither copies whose entries are rounded up or
 // down with a dither: entry e of copy d is rounded up when the fraction of an
 // FP32 unit by which the exact value exceeds its lower FP32 neighbour is above
-// ((d + o_e) mod kDither + 1/2) / kDither, o_e a fixed pseudo-random offset per
-// entry and component, and step k uses copy k mod kDither.  The mean factor
-// over every kDither steps is then exact to 1/(2 kDither) of an FP32 unit while
-// each multiply stays a plain FP32 complex product.  The three radix-16
+// (rev((d + o_e) mod kDither) + 1/2) / kDither, o_e a fixed pseudo-random
+// offset per entry and component, rev the bit reversal of the 8-bit copy
+// number, and step k uses copy k mod kDither.  The mean factor over every
+// kDither (256) steps is then exact to 1/(2 kDither) of an FP32 unit, the rounding
+// alternates up and down within a cycle (bit-reversed thresholds: its partial
+// sums stay within about one unit), and each multiply stays a plain FP32
+// complex product.  The three radix-16
 // constants, applied to most values of every pass and all with the same
 // rounding error, are kept exact to O(eps^2) as unevaluated FP32 pairs
 // (hi + lo, FMA chains): rounded or dithered, their common magnitude error
@@ -107,8 +110,9 @@ template <typename V> __device__ __forceinline__ V cscale(V a, typename real_of<
     return mk<V>(a.x * s, a.y * s);
 }
 
-// copies of each FP32 table (step k uses copy k mod kDither; see above)
-constexpr int kDither = 16;
+// copies of each FP32 table (step k uses copy k mod kDither; see above; a step
+// reads one copy, so the copies cost memory, not cache)
+constexpr int kDither = 256;
 
 // table entry of twiddles and propagator factors: one complex value
 template <typename T> struct tab_of;

@@ -34,6 +34,8 @@ template <typename T> struct ScreenCoef {
     int exact;     // 1: the exact pointwise substep (real gains) instead of the
                    // frozen screen; its absorption number is a = ka u^(K-1)
     T ka;          // (K-1) c_A beta_K dz I_ref^(K-1)
+    int real_gains;  // 1: re_k = re_p = 0 and im_a = 0 (real gains, e.g. the nominal
+                     // ones): the exponent's zero terms are skipped (same values)
 };
 
 template <typename T> __device__ __forceinline__ T ipow(T u, int e) {

@@ -4,8 +4,10 @@
 // budget.  Measurement aid; the paper has no counterpart.
 //
 // Every thread runs kChains independent FMA chains for `iters` rounds, so the
-// pipe never waits on a dependency; the result feeds a store that never
-// happens in practice but that the compiler cannot rule out.
+// pipe never waits on a dependency; the rounds are unrolled kUnroll at a time
+// so that loop control takes a few percent of the issue slots at most; the
+// result feeds a store that never happens in practice but that the compiler
+// cannot rule out.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -15,6 +17,7 @@
 namespace {
 
 constexpr int kChains = 8;
+constexpr int kUnroll = 16;  // rounds per loop trip (iters is rounded up to a multiple)
 constexpr int kProbeThreads = 256;
 
 template <typename T> __global__ void __launch_bounds__(kProbeThreads) k_fma_probe(int iters, T seed, T* sink) {
@@ -23,9 +26,11 @@ template <typename T> __global__ void __launch_bounds__(kProbeThreads) k_fma_pro
     for (int i = 0; i < kChains; ++i) a[i] = seed + (T)(threadIdx.x & 7) + (T)i;
     const T m = (T)0.9999999, c = (T)1e-7;
 #pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
+    for (int it = 0; it < iters; it += kUnroll) {
 #pragma unroll
-        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
     }
     T s = (T)0;
 #pragma unroll
@@ -45,9 +50,12 @@ __global__ void __launch_bounds__(kProbeThreads) k_fma2_probe(int iters, float s
     asm("mov.b64 %0, {%1, %1};" : "=l"(m) : "f"(0.9999999f));
     asm("mov.b64 %0, {%1, %1};" : "=l"(c) : "f"(1e-7f));
 #pragma unroll 1
-    for (int it = 0; it < iters; ++it) {
+    for (int it = 0; it < iters; it += kUnroll) {
 #pragma unroll
-        for (int i = 0; i < kChains; ++i) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[i]) : "l"(m), "l"(c));
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int i = 0; i < kChains; ++i)
+                asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[i]) : "l"(m), "l"(c));
     }
     float s = 0.0f;
 #pragma unroll

@@ -1,9 +1,12 @@
-"""Autotuner for the launch shapes of the march: the column-tile width of the
-single-grid column pass (per grid size and precision) and the block size and
-resident blocks per SM of the persistent batched launch (per size mix).  Each
-candidate is timed on the GPU with CUDA events; the fastest is cached in a JSON
-file (NLSE_TUNE_CACHE, default ~/.cache/paper_2306_15678_gb300/tune.json).
-Results never depend on these choices, only the speed does."""
+"""Autotuner for the launch shapes of the march: the transform radix of the
+row pass (16 or 8 elements per thread) and the column tile of the column pass
+(its width, per-thread or staged by bulk tensor copies, and its transform
+radix) per grid size and precision, and the block size and resident blocks per
+SM of the persistent batched launch (per size mix).  Each candidate is timed on
+the GPU with CUDA events; the fastest is cached in a JSON file
+(NLSE_TUNE_CACHE, default ~/.cache/paper_2306_15678_gb300/tune.json).  For a
+given radix the results do not depend on the tile, bit for bit; the radix
+changes the rounding within the stated tolerances."""
 from __future__ import annotations
 
 import collections
@@ -55,20 +58,23 @@ def _time_ms(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-TILE_CODES = tuple(w | t for t in (0, capi.NLSE_COL_TMA) for w in (1, 2, 4, 8, 16))
+TILE_CODES = tuple(w | t | r for r in (0, capi.NLSE_COL_R8) for t in (0, capi.NLSE_COL_TMA)
+                   for w in (1, 2, 4, 8, 16))
+ROW_RADICES = (16, 8)
 
 
-def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
-              force: bool = False) -> int:
-    """Fastest column-tile code (a width, or'ed with NLSE_COL_TMA for the
-    variant staged by bulk tensor copies) for this grid size and precision."""
+def tune_launch(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
+                force: bool = False) -> dict:
+    """Fastest {"cols": column-tile code, "row_radix": 16 or 8} for this grid
+    size and precision: the column tiles are timed with the default row radix,
+    then the row radices with the chosen tile."""
     path = path or cache_path()
     cache = _load_cache(path)
-    key = f"{_gpu_key()}|grid|{precision}|{int(cfg['n'])}"
+    key = f"{_gpu_key()}|launch|{precision}|{int(cfg['n'])}"
     if key in cache and not force:
-        return int(cache[key]["cols"])
+        return {"cols": int(cache[key]["cols"]), "row_radix": int(cache[key]["row_radix"])}
     U0 = beams.make_field(cfg)
-    best, timings = None, {}
+    best, timings, rtimes = None, {}, {}
     with Grid(cfg, precision=precision) as g:
         g.load(U0).step(2)
         for c in TILE_CODES:
@@ -80,9 +86,33 @@ def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | N
             timings[c] = _time_ms(lambda: g.step(steps), 1) / steps
             if best is None or timings[c] < timings[best]:
                 best = c
-    cache[key] = {"cols": best, "ms_per_step": timings}
+        capi.nlse_set_column_tile(g.h, best)
+        rbest = None
+        for r in ROW_RADICES:
+            try:
+                capi.nlse_set_row_radix(g.h, r)
+            except capi.NlseError:
+                continue
+            g.step(2)
+            rtimes[r] = _time_ms(lambda: g.step(steps), 1) / steps
+            if rbest is None or rtimes[r] < rtimes[rbest]:
+                rbest = r
+    cache[key] = {"cols": best, "row_radix": rbest, "ms_per_step": timings, "row_ms_per_step": rtimes}
     _save_cache(path, cache)
-    return best
+    return {"cols": best, "row_radix": rbest}
+
+
+def apply_launch(g: Grid, launch: dict) -> None:
+    """Set a grid's column tile and row radix to a tune_launch result."""
+    capi.nlse_set_column_tile(g.h, int(launch["cols"]))
+    capi.nlse_set_row_radix(g.h, int(launch["row_radix"]))
+
+
+def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
+              force: bool = False) -> int:
+    """Fastest column-tile code for this grid size and precision (the column
+    part of tune_launch)."""
+    return tune_launch(cfg, precision, steps, path, force)["cols"]
 
 
 def tune_batch(cfgs: list, steps: int = 10, path: str | None = None, force: bool = False,

@@ -62,12 +62,14 @@ def test_every_column_tile_agrees(prec, n, monkeypatch):
 def test_column_tiles_bit_identical(prec, n):
     """The column tile (its width, and per-thread accesses or bulk tensor
     copies) changes which threads transform which column and how the tile
-    reaches shared memory, not the arithmetic: every valid tile gives the
-    same bits, and the staged variant exists at these sizes."""
+    reaches shared memory, not the arithmetic: for one transform radix every
+    valid tile gives the same bits, and the staged variant exists at these
+    sizes.  Each radix (FP32: 16 and 8) stays within 2e-5 of the oracle."""
     cfg = configs.scaled(configs.cfg_dense_fp32(), n, nsteps=2)
     U0 = beams.make_field(cfg)
     if prec == "fp32":
         U0 = U0.astype(np.complex64)
+    ref_or, _, _ = oracle.march(U0.astype(np.complex128), cfg, 3)
     outs = {}
     with Grid(cfg, precision=prec) as g:
         for c in tune.TILE_CODES:
@@ -79,9 +81,40 @@ def test_column_tiles_bit_identical(prec, n):
             outs[c] = g.load(U0).step(3).field()
         assert g.device_status() == capi.NLSE_OK
     assert any(c & capi.NLSE_COL_TMA for c in outs)
-    ref = next(iter(outs.values()))
-    for c, U in outs.items():
-        assert np.array_equal(U, ref), hex(c)
+    if prec == "fp32":
+        assert any(c & capi.NLSE_COL_R8 for c in outs)
+    for radix_bit in (0, capi.NLSE_COL_R8):
+        group = {c: U for c, U in outs.items() if c & capi.NLSE_COL_R8 == radix_bit}
+        if not group:
+            continue
+        ref = next(iter(group.values()))
+        for c, U in group.items():
+            assert np.array_equal(U, ref), hex(c)
+        assert rel_l2(ref, ref_or) < (1e-11 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("n", [8, 64, 512, 4096])
+def test_row_radix_choices_match_oracle(n):
+    """Both FP32 row-pass radices (16 and 8 elements per thread) against the
+    oracle; FP64 grids take radix 8 only."""
+    if n >= 512:
+        cfg = configs.scaled(configs.cfg_dense_fp32(), n, nsteps=2)
+    else:
+        cfg = beam_cfg(n, configs.ALL_TERMS, dz=2.0, L=0.05 * n, w0=0.0125 * n, pcr=30.0)
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    ref, _, _ = oracle.march(U0.astype(np.complex128), cfg, 3)
+    with Grid(cfg, precision="fp32") as g:
+        for r in (16, 8):
+            capi.nlse_set_row_radix(g.h, r)
+            U = g.load(U0).step(3).field()
+            assert rel_l2(U, ref) < 2e-5, (n, r)
+        with pytest.raises(capi.NlseError) as ei:
+            capi.nlse_set_row_radix(g.h, 4)
+        assert ei.value.status == capi.NLSE_EUNSUPPORTED
+    with Grid(cfg, precision="fp64") as g:
+        capi.nlse_set_row_radix(g.h, 8)
+        with pytest.raises(capi.NlseError):
+            capi.nlse_set_row_radix(g.h, 16)
 
 
 def test_staged_column_pass_wait_runs_out_cleanly(monkeypatch):
