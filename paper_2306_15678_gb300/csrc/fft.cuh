@@ -217,12 +217,13 @@ template <int J, bool INV, typename V> __device__ __forceinline__ V w16(V a) {
 }
 
 // FP32 forward W_16^J with packed parts: the same fused operations, in the
-// same order, as the scalar mulc / dotc forms above (the transforms of the
-// march run forward only; the inverse takes the generic form)
-template <int J, bool INV> __device__ __forceinline__ float2 w16(float2 a) {
+// same order, as the scalar mulc / dotc forms above (the forward transforms
+// of the single-line engine; the inverse takes the generic form).  Called by
+// name through w16f, never picked by overload resolution.
+template <int J> __device__ __forceinline__ float2 w16_packed(float2 a) {
     constexpr int j = J & 15;
-    if constexpr (INV || j == 0 || j == 4 || j == 8 || j == 12) {
-        return w16<J, INV, float2>(a);
+    if constexpr (j == 0 || j == 4 || j == 8 || j == 12) {
+        return w16<J, false, float2>(a);
     } else {
         constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173,
                          r2 = 0.70710678118654752440;
@@ -247,6 +248,13 @@ template <int J, bool INV> __device__ __forceinline__ float2 w16(float2 a) {
             return fma2(A, mk<float2>(ch, ch), p);
         }
     }
+}
+
+// W_16^J product used by the butterflies: the packed form for forward FP32
+// transforms, the generic form otherwise
+template <int J, bool INV, typename V> __device__ __forceinline__ V w16f(V a) {
+    if constexpr (std::is_same<V, float2>::value && !INV) return w16_packed<J>(a);
+    else return w16<J, INV, V>(a);
 }
 
 // ----------------------------------------------------------------- DFT_R --
@@ -292,7 +300,7 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V (&a
         // 8 = 2 x 4: even/odd DFT4 then combine with W_8^k = W_16^(2k)
         dft4<INV>(a[0], a[2], a[4], a[6]);
         dft4<INV>(a[1], a[3], a[5], a[7]);
-        V o1 = w16<2, INV>(a[3]), o2 = w16<4, INV>(a[5]), o3 = w16<6, INV>(a[7]);
+        V o1 = w16f<2, INV>(a[3]), o2 = w16f<4, INV>(a[5]), o3 = w16f<6, INV>(a[7]);
         V e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
         a[0] = cadd(e0, a[1]); a[4] = csub(e0, a[1]);
         a[1] = cadd(e1, o1);   a[5] = csub(e1, o1);
@@ -306,9 +314,9 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V (&a
         dft4<INV>(a[2], a[6], a[10], a[14]);
         dft4<INV>(a[3], a[7], a[11], a[15]);
         // after these, a[n2 + 4 k1] holds Y[n2][k1]
-        a[5] = w16<1, INV>(a[5]);  a[9] = w16<2, INV>(a[9]);  a[13] = w16<3, INV>(a[13]);
-        a[6] = w16<2, INV>(a[6]);  a[10] = w16<4, INV>(a[10]); a[14] = w16<6, INV>(a[14]);
-        a[7] = w16<3, INV>(a[7]);  a[11] = w16<6, INV>(a[11]); a[15] = w16<9, INV>(a[15]);
+        a[5] = w16f<1, INV>(a[5]);  a[9] = w16f<2, INV>(a[9]);  a[13] = w16f<3, INV>(a[13]);
+        a[6] = w16f<2, INV>(a[6]);  a[10] = w16f<4, INV>(a[10]); a[14] = w16f<6, INV>(a[14]);
+        a[7] = w16f<3, INV>(a[7]);  a[11] = w16f<6, INV>(a[11]); a[15] = w16f<9, INV>(a[15]);
         dft4<INV>(a[0], a[1], a[2], a[3]);     // k1 = 0 -> X[0], X[4], X[8], X[12]
         dft4<INV>(a[4], a[5], a[6], a[7]);     // k1 = 1 -> X[1], X[5], X[9], X[13]
         dft4<INV>(a[8], a[9], a[10], a[11]);   // k1 = 2

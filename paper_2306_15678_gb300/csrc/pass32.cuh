@@ -336,11 +336,13 @@ __device__ __forceinline__ void col_body32(C2 (&v)[p_e<N / 2, EC>()], C2* sm, co
     for (int half = 0; half < 2; ++half) {
         pr::fft_pair<L, E>(v, sm, tab, j);
         if (half == 0) {
-            // P_x(col) rot / n^2
-            float2 pxr;
-            cmul_1d(rot.x, rot.y, pr::ld1(px + col), pxr.x, pxr.y);
+            // rot / n^2 (a power of two: exact) and P_x(col) = 1 + d + i s, each
+            // applied to every value (their product, rounded once per column,
+            // would carry a magnitude error common to the column's values)
             constexpr float inv_n2 = 1.0f / ((float)N * (float)N);
-            const F2 qx = pr::bc(pxr.x * inv_n2), qy = pr::bc(pxr.y * inv_n2), nqy = pr::bc(-pxr.y * inv_n2);
+            const F2 qx = pr::bc(rot.x * inv_n2), qy = pr::bc(rot.y * inv_n2), nqy = pr::bc(-rot.y * inv_n2);
+            const float2 pxd = pr::ld1(px + col);
+            const F2 xd = pr::bc(pxd.x), xs = pr::bc(pxd.y), nxs = pr::bc(-pxd.y);
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int k = j + m * T;
@@ -352,8 +354,9 @@ __device__ __forceinline__ void col_body32(C2 (&v)[p_e<N / 2, EC>()], C2* sm, co
                 float tr, ti;
                 cmul_1d(orr, oi, w, tr, ti);
                 C2 X = {pr::pk(er + tr, er - tr), pr::pk(ei + ti, ei - ti)};
-                // P_x rot / n^2 (both lanes), then P_y (per lane): X + X (d + i s)
+                // rot / n^2 and P_x (both lanes), then P_y (per lane): X + X (d + i s)
                 X = pr::cmulw(X, qx, qy, nqy);
+                X = {pr::fma(X.re, xd, pr::fma(X.im, nxs, X.re)), pr::fma(X.im, xd, pr::fma(X.re, xs, X.im))};
                 F2 yd, ys;
                 pr::ldw(py + k, yd, ys);
                 X = {pr::fma(X.re, yd, pr::fma(X.im, pr::neg(ys), X.re)), pr::fma(X.im, yd, pr::fma(X.re, ys, X.im))};

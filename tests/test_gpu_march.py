@@ -291,6 +291,28 @@ def test_readouts_match_oracle(prec):
         assert np.array_equal(Ud, g.field())
 
 
+def test_fp32_power_reductions_against_an_fp64_sum_of_the_same_values():
+    """The FP32 stage of the power reductions (per-thread sums and the block
+    tree; the sum across blocks is FP64) against an FP64 sum of the very
+    |U|^2 values the readout produces, on the 4096^2 dense grid after 50 full
+    steps: the readout's power and the march's recorded power (its own
+    partials of the screened field) both within 2e-7 of the FP64 sum."""
+    cfg = configs.cfg_dense_fp32()
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    dx2 = (cfg["L"] / cfg["n"]) ** 2
+    with Grid(cfg, precision="fp32", diag_every=1) as g:
+        g.load(U0).step(50)
+        F = g.fluence().astype(np.float64)
+        exact = math.fsum(F.ravel()) * dx2
+        p_readout = g.power()
+        pw, _ = g.history()
+    err_readout = abs(p_readout / exact - 1)
+    err_march = abs(pw[-1] / exact - 1)  # its values come before the readout's round trip
+    print(f"FP32 reduction stage: readout {err_readout:.2e}, march {err_march:.2e}")
+    assert err_readout <= 2e-7, err_readout
+    assert err_march <= 2e-7, err_march
+
+
 def test_load_from_device_equals_load_from_host():
     cfg = beam_cfg(128, configs.ALL_TERMS, dz=5.0, L=1.28, w0=0.1, pcr=60.0)
     U0 = beams.make_field(cfg)
