@@ -91,14 +91,19 @@ def workload_desc(cfg) -> dict:
     }
 
 
-def csrc_digest() -> str:
-    """Digest of the sources the two march kernels are compiled and launched
-    from (the FFT engine, the pass kernels, the staged column pass and their
-    launch configuration): the DRAM traffic recorded for a kernel is valid
-    while this digest is unchanged."""
+FP32_MARCH_SOURCES = ("dispatch.cuh", "dispatch32.cuh", "fft.cuh", "kernels.cuh", "pair.cuh", "pass32.cuh",
+                      "tma.cuh")
+FP64_MARCH_SOURCES = ("adjoint.cuh", "dispatch.cuh", "fft.cuh", "kernels.cuh", "nlse_f64.cu", "tma.cuh")
+
+
+def csrc_digest(files=FP32_MARCH_SOURCES) -> str:
+    """Digest of the sources the march kernels are compiled and launched from
+    (by default the FP32 march: the FFT engines, the pass kernels, the staged
+    column pass and their launch configuration): counters recorded for a
+    kernel are valid while this digest is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2306_15678_gb300", "csrc")
-    for fn in ("dispatch.cuh", "dispatch32.cuh", "fft.cuh", "kernels.cuh", "pair.cuh", "pass32.cuh", "tma.cuh"):
+    for fn in files:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -277,7 +282,7 @@ def fp64_ops_per_point_step() -> dict | None:
             d = json.load(f)
     except Exception:
         return None
-    return d if d.get("csrc_digest") == csrc_digest() else None
+    return d if d.get("csrc_digest") == csrc_digest(FP64_MARCH_SOURCES) else None
 
 
 def traffic_for(kernel_key: str) -> float | None:
@@ -327,10 +332,29 @@ def bench_batch(args, dev, peak_gbs) -> dict:
     for c in cfgs:
         mix[str(c["n"])] = mix.get(str(c["n"]), 0) + 1
     gbs = 2 * BYTES_PER_PT_PASS * pts * steps / (ms / 1e3) / 1e9
+    # the same beams marched one after another on single grids (autotuned
+    # launch per size; one beam of each size timed, times its count)
+    from paper_2306_15678_gb300.grid import Grid
+    seq_ms = 0.0
+    for n_s, count in mix.items():
+        c0 = next(c for c in cfgs if str(c["n"]) == n_s)
+        launch = tune.tune_launch(c0, "fp32", steps=10)
+        with Grid(c0, precision="fp32", device=dev) as g:
+            tune.apply_launch(g, launch)
+            g.load(fields[cfgs.index(c0)]).step(5)
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(g.stream)
+            g.step(100)
+            a1.record(g.stream)
+            torch.cuda.synchronize(dev)
+            seq_ms += count * a0.elapsed_time(a1) / 100
     return {"workload": f"{len(cfgs)} beams, grid mix {mix}, full screen, FP32, persistent launch "
                         f"under a CUDA graph ({chunk} steps per replay)",
             "value": pts * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
             "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs, "tuning": tuning,
+            "single_grids_ms_per_step": seq_ms, "single_grids_value": pts / (seq_ms / 1e3),
+            "over_single_grids": seq_ms / (ms / steps),
             "status": "ok" if st == 0 else f"status {st}"}
 
 

@@ -362,18 +362,27 @@ typedef struct nlse_batch nlse_batch;
  * Python package).  threads: 256 or 512 threads per block (sets the rows and
  * columns per tile); ctas_per_sm: resident blocks per SM (0 = as many as fit);
  * timeout_ms: bound on every wait; debug_skip_item: test hook -- the work item
- * with this index never reports completion (-1 = none). */
+ * with this index never reports completion (-1 = none); radix: transform
+ * radix of every pass, 16 (or 0: the default; 128 registers per thread) or 8
+ * (64 registers, twice the resident warps; a beam of n = 4096 then needs 512
+ * threads); per_thread_columns: 0 (default) stages the column tiles of beams
+ * with n >= 512 in shared memory with bulk tensor copies, 1 moves every column
+ * tile with per-thread loads and stores.  A batched beam is bit-identical to
+ * the same beam on its own grid with the same radix for its rows and columns
+ * (nlse_set_row_radix, NLSE_COL_R8); the column staging does not change a bit. */
 typedef struct nlse_batch_tuning {
     int32_t threads;
     int32_t ctas_per_sm;
     int32_t timeout_ms;
     int64_t debug_skip_item;
+    int32_t radix;
+    int32_t per_thread_columns;
 } nlse_batch_tuning;
 
 /* Device bytes for `count` beams with parameters params[0..count-1].  No CUDA call. */
 nlse_status nlse_batch_workspace_size(int32_t count, const nlse_params* params, size_t* bytes);
 
-/* Create (tuning may be NULL for the defaults 256, 0, 2000, -1).  Builds every
+/* Create (tuning may be NULL for the defaults 256, 0, 2000, -1, 16, 0).  Builds every
  * beam's tables exactly as nlse_create does.  Synchronises. */
 nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nlse_batch_tuning* tuning,
                               void* cuda_stream, void* dev_workspace, size_t workspace_bytes,

@@ -25,6 +25,8 @@ class Batch:
             t.ctas_per_sm = int(tuning.get("ctas_per_sm", 0))
             t.timeout_ms = int(tuning.get("timeout_ms", 2000))
             t.debug_skip_item = int(tuning.get("debug_skip_item", -1))
+            t.radix = int(tuning.get("radix", 16))
+            t.per_thread_columns = int(tuning.get("per_thread_columns", 0))
         self.ws_bytes = capi.nlse_batch_workspace_size(self.params)
         self._ws, ptr = _aligned_workspace(self.ws_bytes, self.device)
         self.h = capi.nlse_batch_create(self.params, t, self.stream.cuda_stream, ptr, self.ws_bytes)

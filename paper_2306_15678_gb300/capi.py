@@ -50,6 +50,8 @@ class nlse_batch_tuning(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32),
         ("debug_skip_item", ctypes.c_int64),
+        ("radix", ctypes.c_int32),
+        ("per_thread_columns", ctypes.c_int32),
     ]
 
 

@@ -13,10 +13,16 @@
 // NLSE_ETIMEOUT in the status word, raises an abort flag that stops every
 // other block, and returns.
 //
-// Tile bodies are the per-pass kernels' own (row_tile32 / col_tile32 of the
-// pair engine, radix 16), with field accesses that bypass L1 because other SMs rewrite
-// the fields during the launch, so a batched beam is bit-identical to the same
-// beam marched alone.
+// Tile bodies are the per-pass kernels' own (row_tile32 / col_body32 of the
+// pair engine, radix 16 or 8), with field accesses that bypass L1 because
+// other SMs rewrite the fields during the launch, so a batched beam is
+// bit-identical to the same beam marched alone at the same radix.  Column tiles
+// of beams with n >= 512 are moved by bulk tensor copies (as the single grid's
+// staged column pass does, one tensor map per beam in the workspace); the
+// copies read rows that other blocks wrote with ordinary stores and write
+// columns that other blocks read with ordinary loads, so the block orders the
+// two proxies around them (fence.proxy.async) on both sides of the completion
+// counters.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,6 +46,8 @@ struct BatchBeam {
     const float2* px;  // kDitherP copies of n entries each (copy k mod kDitherP serves step k)
     const unsigned char* py;  // kDitherP copies of P_y and the cross-lane factors (py32_copy_bytes)
     const unsigned char* tw;  // kDither twiddle blocks (pass32.cuh: tw32_copy_bytes)
+    const CUtensorMap* map;   // the field as n/2 row pairs x n columns x 4 words, boxes of one
+                              // column x 256 row pairs (staged column tiles; null for n < 512)
     ScreenCoef<float> sc;
     int log2n;
     int col_tiles;
@@ -63,6 +71,7 @@ struct BatchPlan {
     const float2* rot;           // rot[k] = exp(i theta_{k+1}) in FP32 (k: 0-based global step)
     long long timeout_ns;
     long long skip_item;  // test hook: this item never reports completion (-1: none)
+    int staged;           // column tiles of beams with n >= 512 staged by bulk tensor copies
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -71,55 +80,148 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     return v;
 }
 
-// row pairs / columns per tile for a block of THREADS threads
-template <int THREADS, int N> __host__ __device__ constexpr int tile_pairs() { return THREADS / p_tpl<N, 16>(); }
-template <int THREADS, int N> __host__ __device__ constexpr int tile_cols() { return THREADS / p_col_tpl<N, 16>(); }
-template <int THREADS, int N> __host__ __device__ constexpr int batch_row_smem() {
-    return pr::pair_line_stride<N, p_e<N, 16>(), tile_pairs<THREADS, N>()>() * tile_pairs<THREADS, N>() * 16;
+// row pairs / columns per tile for a block of THREADS threads at radix E
+template <int THREADS, int E, int N> __host__ __device__ constexpr int tile_pairs() {
+    return THREADS / p_tpl<N, E>();
 }
-template <int THREADS, int N> __host__ __device__ constexpr bool batch_supported() {
-    return p_tpl<N, 16>() <= THREADS && p_col_tpl<N, 16>() <= THREADS && tile_pairs<THREADS, N>() <= N / 2 &&
-           tile_cols<THREADS, N>() <= N && batch_row_smem<THREADS, N>() <= kMaxSmem &&
-           p_col_smem<N, 16, tile_cols<THREADS, N>()>() <= kMaxSmem;
+template <int THREADS, int E, int N> __host__ __device__ constexpr int tile_cols() {
+    return THREADS / p_col_tpl<N, E>();
 }
-template <int THREADS, int N> __host__ __device__ constexpr int batch_smem() {
-    if constexpr (batch_supported<THREADS, N>())
-        return std::max(batch_row_smem<THREADS, N>(), p_col_smem<N, 16, tile_cols<THREADS, N>()>());
+template <int THREADS, int E, int N> __host__ __device__ constexpr int batch_row_smem() {
+    return pr::pair_line_stride<N, p_e<N, E>(), tile_pairs<THREADS, E, N>()>() * tile_pairs<THREADS, E, N>() * 16;
+}
+template <int THREADS, int E, int N> __host__ __device__ constexpr bool batch_supported() {
+    return p_tpl<N, E>() <= THREADS && p_col_tpl<N, E>() <= THREADS && tile_pairs<THREADS, E, N>() <= N / 2 &&
+           tile_cols<THREADS, E, N>() <= N && batch_row_smem<THREADS, E, N>() <= kMaxSmem - kTmaAlignPad &&
+           p_col_smem<N, E, tile_cols<THREADS, E, N>()>() <= kMaxSmem - kTmaAlignPad;
+}
+// column tiles staged by bulk tensor copies: whole 256-row-pair boxes (n >= 512)
+template <int THREADS, int E, int N> __host__ __device__ constexpr bool batch_staged() {
+    if constexpr (batch_supported<THREADS, E, N>())
+        return p_col_tma_valid<N, E, tile_cols<THREADS, E, N>()>();
+    else
+        return false;
+}
+template <int THREADS, int E, int N> __host__ __device__ constexpr int batch_smem() {
+    if constexpr (batch_supported<THREADS, E, N>())
+        return std::max(batch_row_smem<THREADS, E, N>(), p_col_smem<N, E, tile_cols<THREADS, E, N>()>());
     else
         return 0;
 }
-template <int THREADS> constexpr int batch_smem_max() {
-    return std::max({batch_smem<THREADS, 256>(), batch_smem<THREADS, 512>(), batch_smem<THREADS, 1024>(),
-                     batch_smem<THREADS, 2048>(), batch_smem<THREADS, 4096>()});
+template <int THREADS, int E> constexpr int batch_smem_max() {
+    return std::max({batch_smem<THREADS, E, 256>(), batch_smem<THREADS, E, 512>(), batch_smem<THREADS, E, 1024>(),
+                     batch_smem<THREADS, E, 2048>(), batch_smem<THREADS, E, 4096>()}) +
+           kTmaAlignPad;
 }
 
-// one tile of global step k with the step's table copy, as a single grid applies it
-template <int THREADS, int N>
-__device__ __forceinline__ void batch_tile(const BatchBeam& bm, bool col, int tile, long long k, float2 rot,
-                                           C2* smem) {
-    if constexpr (batch_supported<THREADS, N>()) {
+// Per-block state of the staged column tiles: the block's mbarrier, its phase
+// (kept by thread 0) and a failure flag for the whole block.
+struct StageState {
+    uint64_t* bar;
+    uint32_t parity;
+    int* fail;
+};
+
+// One staged column tile (beam with n >= 512): thread 0 orders the rows other
+// blocks wrote (acquired through the completion counter) before its bulk
+// copies, moves the C columns into their transform lines with one box of 256
+// row pairs per copy and waits for them, bounded; every thread transforms its
+// column exactly as col_tile32 does; thread 0 stores the lines back with bulk
+// copies and waits until those writes are complete, so that the completion
+// signal that follows covers them.  On a wait that runs out the block records
+// bit 1 (and bit 2 if the copies may still be in flight), raises the abort
+// flag and returns false without touching the field.
+template <int THREADS, int E, int N>
+__device__ __forceinline__ bool batch_col_staged(const BatchBeam& bm, int tile, const unsigned char* twb,
+                                                 const float2* px, const float4* py, float2 rot, C2* smem,
+                                                 StageState& st, const BatchPlan& plan) {
+    constexpr int L = N / 2, EE = p_e<L, E>(), T = p_col_tpl<N, E>(), C = tile_cols<THREADS, E, N>();
+    constexpr int LS = pr::pair_line_stride<L, EE, C>(), BOXES = L / kTmaBoxRows;
+    constexpr uint32_t BYTES = (uint32_t)(C * L * 16);
+    const int col0 = tile * C;
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        fence_proxy_async_global();  // the acquired rows, before the copies read them
+        fence_proxy_async_smem();    // this block's earlier use of the lines, before the copies write them
+        mbar_expect_tx(st.bar, BYTES);
+#pragma unroll 1
+        for (int c = 0; c < C; ++c)
+#pragma unroll 1
+            for (int b = 0; b < BOXES; ++b)
+                tma_load_3d(smem + c * LS + b * kTmaBoxRows, bm.map, 0, col0 + c, b * kTmaBoxRows, st.bar);
+        if (!mbar_wait_bounded(st.bar, st.parity)) {
+            atomicOr(plan.status, 2);
+            atomicExch(plan.abort, 1);
+            if (!mbar_wait_bounded(st.bar, st.parity)) atomicOr(plan.status, 4);
+            fail = 1;
+        }
+        st.parity ^= 1u;
+        *st.fail = fail;
+    }
+    __syncthreads();
+    if (*st.fail) return false;  // (uniform)
+    const int c = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
+    C2* line = smem + c * LS;
+    C2 v[EE];
+#pragma unroll
+    for (int m = 0; m < EE; ++m) v[m] = line[j + m * T];
+    __syncthreads();  // the staged tile is consumed; the transforms reuse its memory
+    col_body32<N, E>(v, line, twb, px, py, rot, col0 + c, j);
+#pragma unroll
+    for (int m = 0; m < EE; ++m) line[j + m * T] = v[m];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int cc = 0; cc < C; ++cc)
+#pragma unroll 1
+            for (int b = 0; b < BOXES; ++b)
+                tma_store_3d(bm.map, 0, col0 + cc, b * kTmaBoxRows, smem + cc * LS + b * kTmaBoxRows);
+        tma_store_commit_and_wait();
+        fence_proxy_async_global();  // the copies' writes, before the completion signal
+    }
+    return true;
+}
+
+// one tile of global step k with the step's table copy, as a single grid applies
+// it; false if a staged copy failed (the item then reports no completion)
+template <int THREADS, int E, int N>
+__device__ __forceinline__ bool batch_tile(const BatchBeam& bm, bool col, int tile, long long k, float2 rot,
+                                           C2* smem, StageState& st, const BatchPlan& plan) {
+    if constexpr (batch_supported<THREADS, E, N>()) {
         const int d = (int)(k & (kDither - 1)), dp = (int)(k & (kDitherP - 1));
         const unsigned char* twb = bm.tw + (size_t)d * tw32_copy_bytes(N);
         if (col) {
-            constexpr int C = tile_cols<THREADS, N>();
-            col_tile32<N, 16, C, UnitCG>(bm.field, bm.field, twb, bm.px + (size_t)dp * N,
-                                         reinterpret_cast<const float4*>(bm.py + (size_t)dp * py32_copy_bytes(N)),
-                                         rot, tile * C, smem);
+            constexpr int C = tile_cols<THREADS, E, N>();
+            const float2* px = bm.px + (size_t)dp * N;
+            const float4* py = reinterpret_cast<const float4*>(bm.py + (size_t)dp * py32_copy_bytes(N));
+            if constexpr (batch_staged<THREADS, E, N>()) {
+                if (plan.staged) return batch_col_staged<THREADS, E, N>(bm, tile, twb, px, py, rot, smem, st, plan);
+            }
+            col_tile32<N, E, C, UnitCG>(bm.field, bm.field, twb, px, py, rot, tile * C, smem);
         } else {
-            constexpr int RP = tile_pairs<THREADS, N>();
+            constexpr int RP = tile_pairs<THREADS, E, N>();
             float ts = 0.f, tm = 0.f;
-            row_tile32<N, 16, RP, false, UnitCG>(bm.field, bm.field, twb, bm.sc, tile * RP, smem, ts, tm);
+            row_tile32<N, E, RP, false, UnitCG>(bm.field, bm.field, twb, bm.sc, tile * RP, smem, ts, tm);
         }
     }
+    return true;
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, p_min_blocks<THREADS, 16>()) k_batch_march(BatchPlan plan) {
+// registers: 128 per thread at radix 16, about 85 at radix 8 (the column
+// body's propagator and cross-lane factors on top of the transform)
+template <int THREADS, int E>
+__global__ void __launch_bounds__(THREADS, p_col_min_blocks<THREADS, E>()) k_batch_march(BatchPlan plan) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* smem = reinterpret_cast<C2*>(smraw);
-    __shared__ int s_item_step, s_item_beam, s_item_tile, s_item_col, s_stop;
+    // 128-byte aligned base: the staged column tiles land there by bulk copies
+    const uint32_t pad = (kTmaAlign - (smem_u32(smraw) & (kTmaAlign - 1))) & (kTmaAlign - 1);
+    C2* smem = reinterpret_cast<C2*>(smraw + pad);
+    __shared__ int s_item_step, s_item_beam, s_item_tile, s_item_col, s_stop, s_fail;
     __shared__ float2 s_rot;
     __shared__ long long s_k;
+    __shared__ uint64_t s_bar;
+    if (threadIdx.x == 0 && plan.staged) mbar_init(&s_bar, 1);
+    StageState st{&s_bar, 0u, &s_fail};
     const long long total = (long long)plan.items_per_step * plan.nsteps;
     const int col_total = plan.col_off[plan.nbeams];
     for (;;) {
@@ -175,14 +277,16 @@ __global__ void __launch_bounds__(THREADS, p_min_blocks<THREADS, 16>()) k_batch_
         const float2 rot = s_rot;
         const long long k = s_k;
         const BatchBeam bm = plan.beams[b];
+        bool ok = true;
         switch (bm.log2n) {
-            case 8: batch_tile<THREADS, 256>(bm, col, tile, k, rot, smem); break;
-            case 9: batch_tile<THREADS, 512>(bm, col, tile, k, rot, smem); break;
-            case 10: batch_tile<THREADS, 1024>(bm, col, tile, k, rot, smem); break;
-            case 11: batch_tile<THREADS, 2048>(bm, col, tile, k, rot, smem); break;
-            case 12: batch_tile<THREADS, 4096>(bm, col, tile, k, rot, smem); break;
+            case 8: ok = batch_tile<THREADS, E, 256>(bm, col, tile, k, rot, smem, st, plan); break;
+            case 9: ok = batch_tile<THREADS, E, 512>(bm, col, tile, k, rot, smem, st, plan); break;
+            case 10: ok = batch_tile<THREADS, E, 1024>(bm, col, tile, k, rot, smem, st, plan); break;
+            case 11: ok = batch_tile<THREADS, E, 2048>(bm, col, tile, k, rot, smem, st, plan); break;
+            case 12: ok = batch_tile<THREADS, E, 4096>(bm, col, tile, k, rot, smem, st, plan); break;
             default: break;
         }
+        if (!ok) return;  // (uniform) the abort flag is raised
         __threadfence();  // this thread's tile stores, before the completion signal
         __syncthreads();
         if (threadIdx.x == 0 && item != plan.skip_item)
@@ -207,11 +311,11 @@ int ilog2i(int n) {
     return (1 << k) == n ? k : -1;
 }
 
-template <int THREADS> int tiles_for(int log2n, bool col) {
+template <int THREADS, int E> int tiles_for(int log2n, bool col) {
     auto f = [&](auto nc) -> int {
         constexpr int N = decltype(nc)::value;
-        if constexpr (batch_supported<THREADS, N>())
-            return col ? N / tile_cols<THREADS, N>() : N / 2 / tile_pairs<THREADS, N>();
+        if constexpr (batch_supported<THREADS, E, N>())
+            return col ? N / tile_cols<THREADS, E, N>() : N / 2 / tile_pairs<THREADS, E, N>();
         else return 0;
     };
     switch (log2n) {
@@ -227,7 +331,7 @@ template <int THREADS> int tiles_for(int log2n, bool col) {
 struct BLayout {
     std::vector<size_t> field, px, py;
     size_t tw[kBatchMaxLog2 + 1];
-    size_t beams, col_off, row_off, counters, step_base, rot, partials, readout, scratch, total;
+    size_t maps, beams, col_off, row_off, counters, step_base, rot, partials, readout, scratch, total;
 };
 
 BLayout blayout(int count, const nlse_params* ps) {
@@ -251,6 +355,7 @@ BLayout blayout(int count, const nlse_params* ps) {
         for (int b = 0; b < count; ++b) used |= ps[b].n == (1 << k);
         if (used) { L.tw[k] = o; o = al256(o + (size_t)kDither * tw32_copy_bytes(1 << k)); }
     }
+    L.maps = o;      o = al256(o + sizeof(CUtensorMap) * count);  // 64-byte aligned each
     L.beams = o;     o = al256(o + sizeof(BatchBeam) * count);
     L.col_off = o;   o = al256(o + sizeof(int) * (count + 1));
     L.row_off = o;   o = al256(o + sizeof(int) * (count + 1));
@@ -299,18 +404,18 @@ struct nlse_batch {
 namespace {
 
 
-template <int THREADS> nlse_status plan_tiles(nlse_batch* B) {
+template <int THREADS, int E> nlse_status plan_tiles(nlse_batch* B) {
     for (int b = 0; b < B->count; ++b) {
-        const int tc = tiles_for<THREADS>(B->log2n[b], true), tr = tiles_for<THREADS>(B->log2n[b], false);
+        const int tc = tiles_for<THREADS, E>(B->log2n[b], true), tr = tiles_for<THREADS, E>(B->log2n[b], false);
         if (tc == 0 || tr == 0) return NLSE_EUNSUPPORTED;
         B->col_tiles[b] = tc;
         B->row_tiles[b] = tr;
     }
-    B->smem = batch_smem_max<THREADS>();
+    B->smem = batch_smem_max<THREADS, E>();
     return NLSE_OK;
 }
 
-template <int THREADS> nlse_status launch_batch(nlse_batch* B, int nsteps) {
+template <int THREADS, int E> nlse_status launch_batch(nlse_batch* B, int nsteps) {
     BatchPlan plan;
     unsigned char* ws = B->ws;
     unsigned int* ctr = reinterpret_cast<unsigned int*>(ws + B->lay.counters);
@@ -331,18 +436,30 @@ template <int THREADS> nlse_status launch_batch(nlse_batch* B, int nsteps) {
     plan.rot = reinterpret_cast<const float2*>(ws + B->lay.rot);
     plan.timeout_ns = (long long)B->tune.timeout_ms * 1000000LL;
     plan.skip_item = B->tune.debug_skip_item;
+    plan.staged = B->tune.per_thread_columns ? 0 : 1;
     // reset the work counter, the completion counters and the abort flag (not the status word)
     if (cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * (1 + 2 * B->count), B->stream) != cudaSuccess)
         return NLSE_ECUDA;
     if (cudaMemsetAsync(plan.abort, 0, sizeof(int), B->stream) != cudaSuccess) return NLSE_ECUDA;
-    k_batch_march<THREADS><<<B->grid, THREADS, B->smem, B->stream>>>(plan);
+    k_batch_march<THREADS, E><<<B->grid, THREADS, B->smem, B->stream>>>(plan);
     if (cudaGetLastError() != cudaSuccess) return NLSE_ECUDA;
     k_batch_advance<<<1, 1, 0, B->stream>>>(reinterpret_cast<long long*>(ws + B->lay.step_base), nsteps);
     return cudaGetLastError() == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
 }
 
+// the four launch shapes: threads per block x transform radix
+template <typename F> nlse_status with_shape(const nlse_batch_tuning& t, F&& f) {
+    if (t.threads == 512)
+        return t.radix == 8 ? f(std::integral_constant<int, 512>{}, std::integral_constant<int, 8>{})
+                            : f(std::integral_constant<int, 512>{}, std::integral_constant<int, 16>{});
+    return t.radix == 8 ? f(std::integral_constant<int, 256>{}, std::integral_constant<int, 8>{})
+                        : f(std::integral_constant<int, 256>{}, std::integral_constant<int, 16>{});
+}
+
 nlse_status launch_any(nlse_batch* B, int nsteps) {
-    return B->tune.threads == 512 ? launch_batch<512>(B, nsteps) : launch_batch<256>(B, nsteps);
+    return with_shape(B->tune, [&](auto th, auto e) {
+        return launch_batch<decltype(th)::value, decltype(e)::value>(B, nsteps);
+    });
 }
 
 void advance_host(nlse_batch* B, int nsteps) {
@@ -354,10 +471,14 @@ void advance_host(nlse_batch* B, int nsteps) {
     B->steps += nsteps;
 }
 
-template <int THREADS> nlse_status configure(nlse_batch* B) {
-    auto kern = k_batch_march<THREADS>;
+template <int THREADS, int E> nlse_status configure(nlse_batch* B) {
+    auto kern = k_batch_march<THREADS, E>;
     if (B->smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, B->smem) != cudaSuccess)
+        return NLSE_ECUDA;
+    // as much of the SM's unified memory as shared memory as the blocks can use
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
         return NLSE_ECUDA;
     int dev = 0, sms = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NLSE_ECUDA;
@@ -392,10 +513,13 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     if (reinterpret_cast<uintptr_t>(dev_workspace) & 255) return NLSE_EINVAL;
     BLayout lay = blayout(count, params);
     if (workspace_bytes < lay.total) return NLSE_ENOMEM;
-    nlse_batch_tuning tn = {256, 0, 2000, -1};
+    nlse_batch_tuning tn = {256, 0, 2000, -1, 16, 0};
     if (tuning) tn = *tuning;
+    if (tn.radix == 0) tn.radix = 16;
     if (tn.threads != 256 && tn.threads != 512) return NLSE_EINVAL;
+    if (tn.radix != 16 && tn.radix != 8) return NLSE_EINVAL;
     if (tn.ctas_per_sm < 0 || tn.timeout_ms < 1) return NLSE_EINVAL;
+    if (tn.per_thread_columns != 0 && tn.per_thread_columns != 1) return NLSE_EINVAL;
     nlse_batch* B = new (std::nothrow) nlse_batch();
     if (!B) return NLSE_ENOMEM;
     B->count = count;
@@ -408,12 +532,16 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     B->ws = static_cast<unsigned char*>(dev_workspace);
     B->lay = lay;
     B->tune = tn;
-    st = tn.threads == 512 ? plan_tiles<512>(B) : plan_tiles<256>(B);
-    if (st == NLSE_OK) st = tn.threads == 512 ? configure<512>(B) : configure<256>(B);
+    st = with_shape(tn, [&](auto th, auto e) {
+        constexpr int TH = decltype(th)::value, E = decltype(e)::value;
+        nlse_status r = plan_tiles<TH, E>(B);
+        return r == NLSE_OK ? configure<TH, E>(B) : r;
+    });
     if (st != NLSE_OK) { delete B; return st; }
     // per-beam tables and descriptors (built with the single-grid code so that
     // a batched beam and the same beam alone use identical tables)
     std::vector<BatchBeam> desc(count);
+    std::vector<CUtensorMap> maps(count);
     std::vector<int> coff(count + 1, 0), roff(count + 1, 0);
     bool tw_done[kBatchMaxLog2 + 1] = {};
     for (int b = 0; b < count; ++b) {
@@ -430,6 +558,14 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
         d.px = reinterpret_cast<const float2*>(B->ws + lay.px[b]);
         d.py = B->ws + lay.py[b];
         d.tw = B->ws + lay.tw[B->log2n[b]];
+        d.map = nullptr;
+        if (params[b].n >= 2 * kTmaBoxRows) {
+            if (encode_field_map(&maps[b], d.field, params[b].n, 4, 1) != cudaSuccess) {
+                delete B;
+                return NLSE_ECUDA;
+            }
+            d.map = reinterpret_cast<const CUtensorMap*>(B->ws + lay.maps) + b;
+        }
         d.sc = detail::screen_coef_f32(&params[b]);
         d.log2n = B->log2n[b];
         d.col_tiles = B->col_tiles[b];
@@ -444,6 +580,8 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     if (cudaMemcpyAsync(B->ws + lay.rot, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice,
                         B->stream) != cudaSuccess ||
         cudaMemcpyAsync(B->ws + lay.beams, desc.data(), sizeof(BatchBeam) * count, cudaMemcpyHostToDevice,
+                        B->stream) != cudaSuccess ||
+        cudaMemcpyAsync(B->ws + lay.maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice,
                         B->stream) != cudaSuccess ||
         cudaMemcpyAsync(B->ws + lay.col_off, coff.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
                         B->stream) != cudaSuccess ||
@@ -549,7 +687,7 @@ nlse_status nlse_batch_status(nlse_batch* B) {
         return NLSE_ECUDA;
     if (cudaMemsetAsync(status, 0, sizeof(int), B->stream) != cudaSuccess) return NLSE_ECUDA;
     if (cudaStreamSynchronize(B->stream) != cudaSuccess) return NLSE_ECUDA;
-    if (word[0] & 2) return NLSE_ETIMEOUT;
+    if (word[0] & 6) return NLSE_ETIMEOUT;  // bit 1: a wait ran out; bit 2: a copy may still be in flight
     return NLSE_OK;
 }
 

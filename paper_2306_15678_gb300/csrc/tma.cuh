@@ -97,6 +97,16 @@ __device__ __forceinline__ void tma_store_commit_and_wait_read() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// order this thread's global-memory accesses of the generic proxy (including
+// data it acquired from other threads) with its bulk copies, both ways
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// commit the block's bulk stores and wait until their writes are complete
+__device__ __forceinline__ void tma_store_commit_and_wait() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 
 // The staged tile exists where the column is a whole number of boxes (a box
 // holds kTmaBoxRows row pairs of the state layout, see sidx) and the stage fits

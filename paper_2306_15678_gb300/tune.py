@@ -61,6 +61,7 @@ def _time_ms(fn, reps: int) -> float:
 TILE_CODES = tuple(w | t | r for r in (0, capi.NLSE_COL_R8) for t in (0, capi.NLSE_COL_TMA)
                    for w in (1, 2, 4, 8, 16))
 ROW_RADICES = (16, 8)
+BATCH_RADICES = (16, 8)
 
 
 def tune_launch(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | None = None,
@@ -117,30 +118,32 @@ def tune_grid(cfg: dict, precision: str = "fp32", steps: int = 20, path: str | N
 
 def tune_batch(cfgs: list, steps: int = 10, path: str | None = None, force: bool = False,
                fields: list | None = None) -> dict:
-    """Fastest (threads, ctas_per_sm) for this mix of grid sizes."""
+    """Fastest (threads, radix, ctas_per_sm) for this mix of grid sizes; the
+    column tiles of the beams with n >= 512 are staged (the default)."""
     path = path or cache_path()
     cache = _load_cache(path)
     mix = collections.Counter(int(c["n"]) for c in cfgs)
-    key = f"{_gpu_key()}|batch|" + ",".join(f"{n}x{mix[n]}" for n in sorted(mix))
+    key = f"{_gpu_key()}|batch2|" + ",".join(f"{n}x{mix[n]}" for n in sorted(mix))
     if key in cache and not force:
         return dict(cache[key]["tuning"])
     fields = fields or [beams.make_field(c).astype(np.complex64) for c in cfgs]
     best, timings = None, {}
-    for threads in (256, 512):
-        for per_sm in (1, 2, 3, 4, 0):
-            tuning = {"threads": threads, "ctas_per_sm": per_sm}
-            try:
-                b = Batch(cfgs, tuning)
-            except capi.NlseError:
-                continue
-            with b:
-                for i, U in enumerate(fields):
-                    b.load(i, U)
-                b.step(2)
-                t = _time_ms(lambda: b.step(steps), 1) / steps
-            timings[f"{threads}/{per_sm}"] = t
-            if best is None or t < best[0]:
-                best = (t, tuning)
+    for radix in BATCH_RADICES:
+        for threads in (256, 512):
+            for per_sm in (0, 1, 2):
+                tuning = {"threads": threads, "radix": radix, "ctas_per_sm": per_sm}
+                try:
+                    b = Batch(cfgs, tuning)
+                except capi.NlseError:
+                    continue
+                with b:
+                    for i, U in enumerate(fields):
+                        b.load(i, U)
+                    b.step(2)
+                    t = _time_ms(lambda: b.step(steps), 1) / steps
+                timings[f"{threads}/r{radix}/{per_sm}"] = t
+                if best is None or t < best[0]:
+                    best = (t, tuning)
     cache[key] = {"tuning": best[1], "ms_per_step": timings}
     _save_cache(path, cache)
     return dict(best[1])

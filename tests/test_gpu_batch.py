@@ -24,24 +24,39 @@ def mixed_beams(sizes=(256, 512, 1024, 2048, 512, 4096), seed=11):
     return out
 
 
-def single(cfg, U, nsteps):
+def single(cfg, U, nsteps, radix=16):
     with Grid(cfg, precision="fp32") as g:
+        if radix == 8:
+            capi.nlse_set_row_radix(g.h, 8)
+            capi.nlse_set_column_tile(g.h, capi.NLSE_COL_R8 | 1)
         return g.load(U).step(nsteps).field()
 
 
-@pytest.mark.parametrize("threads", [256, 512])
-def test_batched_beams_bit_identical_to_single_grids(threads):
-    cfgs = mixed_beams()
+@pytest.mark.parametrize("threads,radix,per_thread", [(256, 16, 0), (512, 16, 0), (256, 8, 0), (512, 8, 0),
+                                                      (256, 16, 1), (512, 8, 1)])
+def test_batched_beams_bit_identical_to_single_grids(threads, radix, per_thread):
+    """Every launch shape (threads, radix) and both column paths (staged by
+    bulk tensor copies for n >= 512, or per-thread) give each beam the bits of
+    the same beam on its own grid with the same radix."""
+    sizes = (256, 512, 1024, 2048, 512, 4096) if threads == 512 or radix == 16 else (256, 512, 1024, 2048, 512)
+    cfgs = mixed_beams(sizes)
     fields = [beams.make_field(c).astype(np.complex64) for c in cfgs]
-    with Batch(cfgs, {"threads": threads}) as b:
+    with Batch(cfgs, {"threads": threads, "radix": radix, "per_thread_columns": per_thread}) as b:
         for i, U in enumerate(fields):
             b.load(i, U)
         b.step(7).step(5)
         assert b.status() == capi.NLSE_OK
         assert b.steps_taken == 12
         for i, (c, U) in enumerate(zip(cfgs, fields)):
-            assert np.array_equal(b.field(i), single(c, U, 12)), i
+            assert np.array_equal(b.field(i), single(c, U, 12, radix)), i
             assert np.array_equal(b.field(i, device=True).cpu().numpy(), b.field(i))
+
+
+def test_radix8_batch_rejects_4096_at_256_threads():
+    cfgs = mixed_beams((4096,))
+    with pytest.raises(capi.NlseError) as ei:
+        Batch(cfgs, {"threads": 256, "radix": 8})
+    assert ei.value.status == capi.NLSE_EUNSUPPORTED
 
 
 def test_graph_replay_equals_eager_steps():
@@ -103,13 +118,16 @@ def test_batch_rejects_unsupported_inputs():
     with pytest.raises(capi.NlseError) as ei:
         Batch(cfgs, {"threads": 384})
     assert ei.value.status == capi.NLSE_EINVAL
+    with pytest.raises(capi.NlseError) as ei:
+        Batch(cfgs, {"radix": 4})
+    assert ei.value.status == capi.NLSE_EINVAL
 
 
 def test_autotuner_picks_a_valid_shape(tmp_path):
     from paper_2306_15678_gb300 import tune
     cfgs = mixed_beams((512, 1024))
     t = tune.tune_batch(cfgs, steps=3, path=str(tmp_path / "t.json"))
-    assert t["threads"] in (256, 512)
+    assert t["threads"] in (256, 512) and t["radix"] in (16, 8)
     assert tune.tune_batch(cfgs, path=str(tmp_path / "t.json")) == t  # cached
     c = tune.tune_grid(configs.scaled(configs.cfg_dense_fp32(), 1024), "fp32", steps=3,
                        path=str(tmp_path / "t.json"))
