@@ -85,7 +85,8 @@ template <int THREADS, int E> __host__ __device__ constexpr int p_col_min_blocks
 // outputs of pass 1.  The residual error of a dithered factor over a cycle,
 // up to 1/(2 kDither) of an FP32 unit, then changes the power coherently from
 // cycle to cycle: with 16 copies the Kerr-only power drifted by 2e-6 over the
-// 856 steps to the first collapse at 4096^2, with 256 by a sixteenth of that.
+// 856 steps to the first collapse at 4096^2; with 256 (and P_x applied to each
+// value, see col_body32) it stays within 1e-6.
 constexpr int kDitherP = kDither;
 __host__ __device__ constexpr size_t py32_copy_bytes(int n) { return (size_t)16 * (n / 2) + (size_t)8 * (n / 2); }
 __host__ __device__ constexpr int tw32_min(int a, int b) { return a < b ? a : b; }
