@@ -5,9 +5,10 @@ oracle on the same input bytes.
 
 "Before the first filament collapse" is read as up to the first step whose peak
 reaches w_pf = 2 TW/cm^2 (Sec. 2, before Eq. 4).  The GPU's own peak history
-locates that step first; the fluence is then compared every 16 steps (one cycle
-of the 16 dithered table copies, so that every copy is exercised between two
-comparisons) and at the collapse step itself, over at least 64 steps.
+locates that step first; the fluence is then compared every 16 steps and at the
+collapse step itself, over at least 64 steps.  The run to the collapse (856
+steps) goes through every one of the 256 dithered copies of the FP32 tables
+(step k uses copy k mod 256) three times.
 
 Tolerances: fluence rel-L2 <= 2e-4 (full screen); in the lossless Kerr-only run,
 the field itself, rel-L2 <= 2e-4, and the power drift <= 1e-6.
