@@ -70,7 +70,7 @@ def compare_until_collapse(cfg, field: bool):
     return stop, errs, pw, P0, gpk
 
 
-def test_fp32_headline_grid_fluence_every_dither_cycle_until_first_collapse():
+def test_fp32_headline_grid_fluence_every_16_steps_until_first_collapse():
     cfg = configs.cfg_dense_fp32()
     stop, errs, _, _, gpk = compare_until_collapse(cfg, field=False)
     print(f"first collapse at step {stop}; (step, fluence rel-L2, oracle peak): {errs}")
