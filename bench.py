@@ -603,6 +603,9 @@ def main():
         g_clk.close()
         # replicas: sum of every rank's point-steps over the slowest rank's time
         value, ms = shard.aggregate(float(n * n * args.steps), ms, dist, dev)
+        if clk is not None and clk.get("sm_mhz"):
+            # clock-normalised step: SM cycles per step at the median clock under load
+            clk["sm_cycles_per_step"] = ms / args.steps * 1e3 * clk["sm_mhz"]
 
         # ---- per-kernel times for the roofline (events around every launch)
         kroof = min(args.steps, 500)
@@ -620,6 +623,8 @@ def main():
         if dom == "column pass":
             radix = 8 if cols & capi.NLSE_COL_R8 else 16
             kkey = f"{'k_col_pass32_tma' if cols & capi.NLSE_COL_TMA else 'k_col_pass32'}<{n},{radix},{cols & 0xff}>"
+        elif launch["row_radix"] & capi.NLSE_ROW_STAGED:
+            kkey = f"k_row_pass32_pf<{n},diag>"
         else:
             kkey = f"k_row_pass32<{n},{launch['row_radix']},diag>"
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",

@@ -190,9 +190,15 @@ nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols);
 /* Radix of the row pass's transforms: 16 (16 elements per thread, the default
  * in FP32) or 8 (8 elements per thread: twice the threads in flight, one more
  * shared-memory exchange per transform); FP64 grids take 8 only.
- * NLSE_EUNSUPPORTED otherwise.  Chosen by the autotuner with the column tile;
- * the radix changes the rounding, not the tolerances met.  Finalises pending
- * diagnostics first (enqueued on the grid's stream). */
+ * NLSE_ROW_STAGED | 16 (FP32, n >= 2048): radix 16 with persistent blocks, each
+ * moving its next row pair into shared memory with one bulk copy while it
+ * finishes the current one; bit-identical to radix 16, its wait for a copy
+ * bounded as the staged column pass's (NLSE_ETIMEOUT, see
+ * nlse_set_column_tile).  NLSE_EUNSUPPORTED otherwise.  Chosen by the
+ * autotuner with the column tile; the radix changes the rounding, not the
+ * tolerances met.  Finalises pending diagnostics first (enqueued on the grid's
+ * stream). */
+enum { NLSE_ROW_STAGED = 0x100 };
 nlse_status nlse_set_row_radix(nlse_grid* g, int32_t radix);
 
 /* Number of z steps taken since the last load. */

@@ -16,6 +16,7 @@ NLSE_OK, NLSE_EINVAL, NLSE_EUNSUPPORTED, NLSE_ENOMEM = 0, 1, 2, 3
 NLSE_ECUDA, NLSE_ENONFINITE, NLSE_ETIMEOUT, NLSE_ESTATE = 4, 5, 6, 7
 NLSE_COL_TMA = 0x100  # column tile staged with bulk tensor copies (or'ed with the width)
 NLSE_COL_R8 = 0x200  # radix-8 column transform (FP32; or'ed with the tile code)
+NLSE_ROW_STAGED = 0x100  # persistent row pass staging each row pair by a bulk copy (FP32, | 16)
 NLSE_LIE, NLSE_STRANG = 0, 1  # splitting of a step
 NLSE_EXACT_SCREEN = 2  # or'ed into the scheme: exact pointwise substep instead of the frozen screen
 NLSE_KERR, NLSE_PLASMA, NLSE_MPA, NLSE_DIFFRACTION, NLSE_ALL_TERMS = 1, 2, 4, 8, 15

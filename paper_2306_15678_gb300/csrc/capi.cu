@@ -500,7 +500,8 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
             sc.reps = 1;
             sc.scale = (T)1 / (T)n;
             if (ks->row_pass(field, field, twiddles_at<T>(g->ws + g->lay.tw, n, k), sc, partials, false,
-                             g->row_radix, g->stream) != cudaSuccess)
+                             g->row_radix, reinterpret_cast<int*>(g->ws + g->lay.status), g->stream) !=
+                cudaSuccess)
                 return NLSE_ECUDA;
             sc.scale = (T)1;
         }
@@ -519,7 +520,8 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
         // diag buffer; a full buffer is finalised into the history in one launch
         double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * row_parts(ks, g->row_radix);
         sc.reps = strang && s + 1 < nsteps ? 2 : 1;
-        e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->row_radix, g->stream);
+        e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->row_radix,
+                         reinterpret_cast<int*>(g->ws + g->lay.status), g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (diag && ++g->diag_pending == kDiagBatch && flush_diag<T>(g) != NLSE_OK) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -908,7 +910,7 @@ nlse_status nlse_set_column_tile(nlse_grid* g, int32_t cols) {
 nlse_status nlse_set_row_radix(nlse_grid* g, int32_t radix) {
     if (!g) return NLSE_EINVAL;
     const int mask = g->p.precision == NLSE_FP64 ? g->k64->row_radix_mask : g->k32->row_radix_mask;
-    const int bit = radix == 16 ? 1 : radix == 8 ? 2 : 0;
+    const int bit = radix == 16 ? 1 : radix == 8 ? 2 : radix == (kRowStaged | 16) ? 4 : 0;
     if (!(mask & bit)) return NLSE_EUNSUPPORTED;
     // recorded partials carry the block count of the radix they were made with
     if (flush_diag_any(g) != NLSE_OK) return NLSE_ECUDA;
@@ -1345,7 +1347,7 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
                          py_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols, nullptr,
                          0u, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (ks->row_pass(state, state, tws, sc, partials, false, a->row_radix, a->stream) != cudaSuccess)
+        if (ks->row_pass(state, state, tws, sc, partials, false, a->row_radix, nullptr, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
     }
     double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
@@ -1388,7 +1390,7 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
                              nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             if (s + 1 < c1 &&
-                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->row_radix, a->stream) !=
+                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->row_radix, nullptr, a->stream) !=
                     cudaSuccess)
                 return NLSE_ECUDA;
         }

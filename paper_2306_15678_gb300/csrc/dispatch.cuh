@@ -20,6 +20,9 @@ constexpr int kMaxSmem = 232448;  // 227 KB opt-in shared memory per block (sm_1
 // radix 16 without it)
 constexpr int kColTma = 0x100;
 constexpr int kColR8 = 0x200;
+// row-pass code: radix 16 with persistent blocks that stage each row pair by a
+// bulk copy (pass32.cuh: k_row_pass32_pf), or'ed with the radix
+constexpr int kRowStaged = 0x100;
 constexpr int kColOptionCount = 20;
 constexpr int kColOptions[kColOptionCount] = {
     1, 2, 4, 8, 16, kColTma | 1, kColTma | 2, kColTma | 4, kColTma | 8, kColTma | 16,
@@ -35,11 +38,13 @@ template <typename T> struct KernelSet {
     int adj_blocks;    // blocks (partials) of the loss seed and the backward row pass
     int col_mask;      // bit i set: column tile kColOptions[i] is instantiated
     int col_default;   // default column tile
-    int row_radix_mask;     // bit 0: radix 16 available for the row pass, bit 1: radix 8
+    int row_radix_mask;     // bit 0: radix 16 available for the row pass, bit 1: radix 8,
+                            // bit 2: radix 16 with staged persistent blocks (kRowStaged | 16)
     int row_radix_default;  // default radix of the row pass (16 or 8)
-    // rad: radix of the row transform (16 or 8; FP64: 8)
+    // rad: row-pass code (16, 8 or kRowStaged | 16; FP64: 8); status: device
+    // status word (bit 1: a bounded wait ran out), may be null
     cudaError_t (*row_pass)(const V* src, V* dst, const W* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, int rad, cudaStream_t s);
+                            bool diag, int rad, int* status, cudaStream_t s);
     // status: device status word (bit 1: a bounded wait ran out), may be null;
     // extra_tx: test hook of the staged variant (0 in use)
     cudaError_t (*col_pass)(const V* src, V* dst, const W* tw, const W* px, const W* py, W rot,
@@ -128,7 +133,7 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, int smem, cu
 template <typename T, int N>
 cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
                             const typename tab_of<T>::type* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, int, cudaStream_t s) {
+                            bool diag, int, int*, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
     cudaError_t e;

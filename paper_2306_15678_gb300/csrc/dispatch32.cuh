@@ -38,11 +38,51 @@ cudaError_t launch_row_pass32_e(const float2* src, float2* dst, const float2* tw
     }
     return e != cudaSuccess ? e : cudaGetLastError();
 }
+// the persistent staged row pass exists where a row pair fills whole warps of one block
+template <int N> constexpr bool p_row_staged_ok() { return p_rows<N, 16>() == 1 && p_tpl<N, 16>() % 32 == 0; }
+
+// blocks of the persistent row pass: as many as are resident at once
+inline int resident_grid(int per_sm, int units) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return units;
+    if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return units;
+    const long long g = (long long)sms[dev] * per_sm;
+    return g < units ? (int)g : units;
+}
+
+template <int N>
+cudaError_t launch_row_pass32_pf(const float2* src, float2* dst, const float2* tw, ScreenCoef<float> sc,
+                                 double* partials, bool diag, int* status, cudaStream_t s) {
+    if constexpr (p_row_staged_ok<N>()) {
+        constexpr int THREADS = p_tpl<N, 16>(), SMEM = p_row_smem<N, 16>();
+        constexpr int RES = p_min_blocks<THREADS, 16>();
+        const float4* in = reinterpret_cast<const float4*>(src);
+        float4* out = reinterpret_cast<float4*>(dst);
+        const int grid = resident_grid(RES, N / 2);
+        cudaError_t e;
+        if (diag) {
+            if ((e = ensure_smem_carveout<k_row_pass32_pf<N, true>>(SMEM, RES)) != cudaSuccess) return e;
+            e = launch_pdl(k_row_pass32_pf<N, true>, dim3(grid), dim3(THREADS), SMEM, s, in, out, twb_of(tw), sc,
+                           partials, status);
+        } else {
+            if ((e = ensure_smem_carveout<k_row_pass32_pf<N, false>>(SMEM, RES)) != cudaSuccess) return e;
+            e = launch_pdl(k_row_pass32_pf<N, false>, dim3(grid), dim3(THREADS), SMEM, s, in, out, twb_of(tw), sc,
+                           partials, status);
+        }
+        return e != cudaSuccess ? e : cudaGetLastError();
+    } else {
+        return cudaErrorInvalidConfiguration;
+    }
+}
+
 template <int N>
 cudaError_t launch_row_pass32(const float2* src, float2* dst, const float2* tw, ScreenCoef<float> sc,
-                              double* partials, bool diag, int rad, cudaStream_t s) {
+                              double* partials, bool diag, int rad, int* status, cudaStream_t s) {
     if (rad == 16) return launch_row_pass32_e<N, 16>(src, dst, tw, sc, partials, diag, s);
     if (rad == 8) return launch_row_pass32_e<N, 8>(src, dst, tw, sc, partials, diag, s);
+    if (rad == (kRowStaged | 16)) return launch_row_pass32_pf<N>(src, dst, tw, sc, partials, diag, status, s);
     return cudaErrorInvalidConfiguration;
 }
 
@@ -192,7 +232,7 @@ template <int N> KernelSet<float> make_set32() {
     k.adj_blocks = N / rows_per_block<float, N>();
     k.col_mask = col_mask32<N>();
     k.col_default = col_default32<N>();
-    k.row_radix_mask = 3;
+    k.row_radix_mask = 3 | (p_row_staged_ok<N>() ? 4 : 0);
     k.row_radix_default = 16;
     k.row_pass = &launch_row_pass32<N>;
     k.col_pass = &launch_col_pass32<N>;

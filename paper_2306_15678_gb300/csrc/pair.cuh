@@ -234,11 +234,19 @@ template <int I, int END, typename F> __device__ __forceinline__ void sfor(F&& f
     }
 }
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // Forward transform of a pair of lines of length L held in v (layout above).
 // `sm` is this group's padded line (pair_padded_len<L, E>() slots); every
-// thread of the block must call this (it contains __syncthreads()).
-template <int L, int E, int NS = 1>
-__device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __restrict__ tab, int j) {
+// thread of the block must call this (it contains __syncthreads()).  `hook`
+// runs at the start of the last pass of a transform with more than one pass,
+// when every thread has read the line for the last time: from there on the
+// line is free until the transform returns.
+template <int L, int E, int NS = 1, class H = NoHook>
+__device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __restrict__ tab, int j,
+                                         const H& hook = H{}) {
     constexpr int REM = L / NS;
     constexpr int R = REM >= E ? E : REM;
     constexpr bool LAST = (NS * R == L);
@@ -249,6 +257,7 @@ __device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __res
     static_assert(R == 1 || R == 2 || R == 4 || R == 8 || R == 16, "radix");
     constexpr int TA = pair_tab_offset(L, E, NS);  // sub-pass A entries
     constexpr int TB = TA + (R1 - 1) * NS;         // sub-pass B entries
+    if constexpr (LAST && NS > 1) hook();
 #pragma unroll
     for (int i = 0; i < B; ++i) {
         const int b = j + i * T;
@@ -316,7 +325,7 @@ __device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __res
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = sm[padix<E>(j + m * T)];
         __syncthreads();
-        fft_pair<L, E, NS * R>(v, sm, tab, j);
+        fft_pair<L, E, NS * R>(v, sm, tab, j, hook);
     }
 }
 

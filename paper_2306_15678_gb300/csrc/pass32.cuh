@@ -238,26 +238,21 @@ __device__ __forceinline__ C2 apply_screen2(C2 v, const ScreenCoef<float>& c, un
 
 // ------------------------------------------------------------- row tile --
 
-// Row pass body for the row pairs pair0 .. pair0 + p_rows - 1 (group g of
-// p_tpl threads per pair): v = B_x S, screen(s), S = F_x U; with DIAG adds
-// the thread's sum and max of |U|^2 (after the first screen).
-template <int N, int ER, int RP, bool DIAG, class M>
-__device__ __forceinline__ void row_tile32(const float4* src, float4* dst, const unsigned char* twb,
-                                           const ScreenCoef<float>& sc, int pair0, C2* smem, float& tsum,
-                                           float& tmax) {
-    constexpr int E = p_e<N, ER>(), T = p_tpl<N, ER>();
-    constexpr int LS = pr::pair_line_stride<N, E, RP>();
-    const int g = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
-    const size_t row = (size_t)(pair0 + g) * N;
-    C2* sm = smem + g * LS;
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, ER));
-    C2 v[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = pr::swp(M::ld(src + row + j + m * T));  // B_x = swap F_x swap
+// Row pass transforms of one row pair held in v (B_x S swapped in): B_x,
+// screen(s), F_x; with DIAG adds the thread's sum and max of |U|^2 (after the
+// first screen); EXACT compiles the exact pointwise substep in.  hook runs in
+// the forward transform once the line is free (pair.cuh: fft_pair).
+template <int N, int ER, bool DIAG, bool EXACT = true, class H = pr::NoHook>
+__device__ __forceinline__ void row_body32(C2 (&v)[p_e<N, ER>()], C2* sm, const float4* __restrict__ tab,
+                                           const ScreenCoef<float>& sc, int j, float& tsum, float& tmax,
+                                           const H& hook = H{}) {
+    constexpr int E = p_e<N, ER>();
     F2 fsum = pr::bc(0.0f);
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
-        pr::fft_pair<N, E>(v, sm, tab, j);
+        pr::fft_pair<N, E>(v, sm, tab, j, [&]() {
+            if (half == 1) hook();
+        });
         if (half == 0) {
             // the field entering the screen, swapped back
 #pragma unroll
@@ -271,7 +266,7 @@ __device__ __forceinline__ void row_tile32(const float4* src, float4* dst, const
 #pragma unroll 1
             for (int rep = 0; rep < sc.reps; ++rep) {
                 if (sc.active) {
-                    if (M::kExactScreen && sc.exact) {  // (uniform)
+                    if (EXACT && sc.exact) {  // (uniform)
 #pragma unroll
                         for (int m = 0; m < E; ++m) {
                             float r0, r1, i0, i1;
@@ -302,6 +297,25 @@ __device__ __forceinline__ void row_tile32(const float4* src, float4* dst, const
         }
     }
     if (DIAG) tsum += pr::lo(fsum) + pr::hi(fsum);
+}
+
+// Row pass body for the row pairs pair0 .. pair0 + p_rows - 1 (group g of
+// p_tpl threads per pair): v = B_x S, screen(s), S = F_x U; with DIAG adds
+// the thread's sum and max of |U|^2 (after the first screen).
+template <int N, int ER, int RP, bool DIAG, class M>
+__device__ __forceinline__ void row_tile32(const float4* src, float4* dst, const unsigned char* twb,
+                                           const ScreenCoef<float>& sc, int pair0, C2* smem, float& tsum,
+                                           float& tmax) {
+    constexpr int E = p_e<N, ER>(), T = p_tpl<N, ER>();
+    constexpr int LS = pr::pair_line_stride<N, E, RP>();
+    const int g = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
+    const size_t row = (size_t)(pair0 + g) * N;
+    C2* sm = smem + g * LS;
+    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, ER));
+    C2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = pr::swp(M::ld(src + row + j + m * T));  // B_x = swap F_x swap
+    row_body32<N, ER, DIAG, M::kExactScreen>(v, sm, tab, sc, j, tsum, tmax);
 #pragma unroll
     for (int m = 0; m < E; ++m) M::st(dst + row + j + m * T, v[m]);
 }
@@ -390,6 +404,99 @@ k_row_pass32(const float4* src, float4* dst, const unsigned char* twb, ScreenCoe
     row_tile32<N, ER, p_rows<N, ER>(), DIAG, UnitPlain>(src, dst, twb, sc, blockIdx.x * p_rows<N, ER>(),
                                                          reinterpret_cast<C2*>(smraw), tsum, tmax);
     if constexpr (DIAG) block_partials<float>(tsum, tmax, partials);
+}
+
+// One contiguous bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global into shared memory, counted in bytes on bar; the calling
+// thread also arms bar for those bytes.
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    mbar_expect_tx(bar, bytes);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// block_partials<float> (kernels.cuh) for partial slot `slot`, usable again by
+// the same block: the same reduction order, so the same bits.
+__device__ __forceinline__ void block_partials32_at(float tsum, float tmax, double* __restrict__ partials, int slot) {
+    __shared__ float red_s[32];
+    __shared__ float red_m[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red_s[warp] = tsum; red_m[warp] = tmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        float ss = 0.0f, mm = 0.0f;
+        for (int w = 0; w < nw; ++w) { ss += red_s[w]; mm = fmaxf(mm, red_m[w]); }
+        partials[2 * slot] = (double)ss;
+        partials[2 * slot + 1] = (double)mm;
+    }
+    __syncthreads();  // red_s / red_m are free again
+}
+
+// Row pass with persistent blocks (one row pair per block at a time, n >= 2048
+// at radix 16): block b takes row pairs b, b + G, b + 2G, ... (G blocks).  A
+// row pair is n contiguous units, so it is moved into the block's transform
+// line by one bulk copy; the copy for the next row pair is issued as soon as
+// the forward transform has read the line for the last time, and lands while
+// the last transform pass, the stores and the partials of the current row
+// pair run.  Arithmetic, stores and partials (one slot per row pair) are those
+// of k_row_pass32 at radix 16, bit for bit.  The wait for a copy is bounded as
+// in the staged column pass (status bits 2 and 4, tma.cuh).
+template <int N, bool DIAG>
+__global__ void __launch_bounds__(p_tpl<N, 16>(), p_min_blocks<p_tpl<N, 16>(), 16>())
+k_row_pass32_pf(const float4* src, float4* dst, const unsigned char* twb, ScreenCoef<float> sc,
+                double* __restrict__ partials, int* __restrict__ status) {
+    constexpr int E = p_e<N, 16>(), T = p_tpl<N, 16>(), NP = N / 2;
+    constexpr uint32_t BYTES = (uint32_t)N * 16;
+    static_assert(p_rows<N, 16>() == 1 && T % 32 == 0, "one row pair of whole warps per block");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint64_t bar;
+    __shared__ int s_fail;
+    C2* line = reinterpret_cast<C2*>(smraw);
+    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, 16));
+    const int j = (int)threadIdx.x;
+    pdl_trigger();
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        mbar_init(&bar, 1);
+        if ((int)blockIdx.x < NP) bulk_load_1d(line, src + (size_t)blockIdx.x * N, BYTES, &bar);
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+#pragma unroll 1
+    for (int p = blockIdx.x; p < NP; p += gridDim.x) {
+        if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, parity)) {
+            if (status) atomicOr(status, 2);
+            // the copy still targets this block's memory: wait for it once more
+            if (!mbar_wait_bounded(&bar, parity) && status) atomicOr(status, 4);
+            s_fail = 1;
+        }
+        parity ^= 1u;
+        __syncthreads();
+        if (s_fail) return;  // (uniform)
+        C2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = pr::swp(line[j + m * T]);  // B_x = swap F_x swap
+        __syncthreads();  // the transforms' exchanges reuse the line
+        const int next = p + (int)gridDim.x;
+        float tsum = 0.0f, tmax = 0.0f;
+        row_body32<N, 16, DIAG>(v, line, tab, sc, j, tsum, tmax, [&]() {
+            if (threadIdx.x == 0 && next < NP) {
+                fence_proxy_async_smem();  // the exchanges' accesses of the line, before the copy's writes
+                bulk_load_1d(line, src + (size_t)next * N, BYTES, &bar);
+            }
+        });
+#pragma unroll
+        for (int m = 0; m < E; ++m) UnitPlain::st(dst + (size_t)p * N + j + m * T, v[m]);
+        if constexpr (DIAG) block_partials32_at(tsum, tmax, partials, p);
+    }
 }
 
 // Column tile with per-thread unit loads and stores: C columns from col0

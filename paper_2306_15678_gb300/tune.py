@@ -60,7 +60,7 @@ def _time_ms(fn, reps: int) -> float:
 
 TILE_CODES = tuple(w | t | r for r in (0, capi.NLSE_COL_R8) for t in (0, capi.NLSE_COL_TMA)
                    for w in (1, 2, 4, 8, 16))
-ROW_RADICES = (16, 8)
+ROW_RADICES = (16, 8, capi.NLSE_ROW_STAGED | 16)
 BATCH_RADICES = (16, 8)
 
 
@@ -71,7 +71,7 @@ def tune_launch(cfg: dict, precision: str = "fp32", steps: int = 20, path: str |
     then the row radices with the chosen tile."""
     path = path or cache_path()
     cache = _load_cache(path)
-    key = f"{_gpu_key()}|launch|{precision}|{int(cfg['n'])}"
+    key = f"{_gpu_key()}|launch2|{precision}|{int(cfg['n'])}"
     if key in cache and not force:
         return {"cols": int(cache[key]["cols"]), "row_radix": int(cache[key]["row_radix"])}
     U0 = beams.make_field(cfg)

@@ -104,17 +104,47 @@ def test_row_radix_choices_match_oracle(n):
     U0 = beams.make_field(cfg).astype(np.complex64)
     ref, _, _ = oracle.march(U0.astype(np.complex128), cfg, 3)
     with Grid(cfg, precision="fp32") as g:
-        for r in (16, 8):
+        for r in (16, 8) + ((capi.NLSE_ROW_STAGED | 16,) if n >= 2048 else ()):
             capi.nlse_set_row_radix(g.h, r)
             U = g.load(U0).step(3).field()
             assert rel_l2(U, ref) < 2e-5, (n, r)
         with pytest.raises(capi.NlseError) as ei:
             capi.nlse_set_row_radix(g.h, 4)
         assert ei.value.status == capi.NLSE_EUNSUPPORTED
+        if n < 2048:  # the staged row pass needs one row pair of whole warps per block
+            with pytest.raises(capi.NlseError) as ei:
+                capi.nlse_set_row_radix(g.h, capi.NLSE_ROW_STAGED | 16)
+            assert ei.value.status == capi.NLSE_EUNSUPPORTED
     with Grid(cfg, precision="fp64") as g:
         capi.nlse_set_row_radix(g.h, 8)
         with pytest.raises(capi.NlseError):
             capi.nlse_set_row_radix(g.h, 16)
+        with pytest.raises(capi.NlseError):
+            capi.nlse_set_row_radix(g.h, capi.NLSE_ROW_STAGED | 16)
+
+
+@pytest.mark.parametrize("n", [2048, 4096, 8192])
+@pytest.mark.parametrize("scheme", ["lie", "strang"])
+def test_staged_row_pass_bit_identical_to_radix16(n, scheme):
+    """The persistent row pass that stages each row pair by a bulk copy gives
+    the bits of the radix-16 row pass: the field and the per-step power and
+    peak history (one partial per row pair in both), Lie and Strang steps
+    (whose opening half screen runs the row pass alone)."""
+    cfg = configs.scaled(configs.cfg_dense_fp32(), n, nsteps=5)
+    if scheme == "strang":
+        cfg = dict(cfg, scheme="strang")
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    out = {}
+    for r in (16, capi.NLSE_ROW_STAGED | 16):
+        with Grid(cfg, precision="fp32", diag_every=1) as g:
+            capi.nlse_set_row_radix(g.h, r)
+            g.load(U0).step(2).step(3)
+            pw, pk = g.history()
+            out[r] = (g.field(), pw, pk)
+            assert g.device_status() == capi.NLSE_OK
+    a, b = out[16], out[capi.NLSE_ROW_STAGED | 16]
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
 def test_staged_column_pass_wait_runs_out_cleanly(monkeypatch):
