@@ -439,7 +439,7 @@ def bench_large_adjoint(dev, nsteps: int) -> dict:
     import numpy as np
     import torch
 
-    from paper_2306_15678_gb300 import beams, configs
+    from paper_2306_15678_gb300 import beams, configs, tune
     from paper_2306_15678_gb300.adjoint import AdjointMarch
     from paper_2306_15678_gb300.grid import Grid
     cfg = configs.cfg_large_adjoint(1)[0]
@@ -450,7 +450,9 @@ def bench_large_adjoint(dev, nsteps: int) -> dict:
     D = torch.from_numpy(np.abs(beams.make_field(dict(cfg, beam=dict(cfg["beam"], w0=3.06, seed=5099)))) ** 2).to(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        launch = tune.tune_launch(cfg, "fp32", steps=5)  # the same launch shape for both arms
         with Grid(cfg, precision="fp32", device=dev, stream=stream) as g:
+            tune.apply_launch(g, launch)
             g.load(U0).step(3)
             g.load(U0)
             torch.cuda.synchronize(dev)
@@ -462,6 +464,7 @@ def bench_large_adjoint(dev, nsteps: int) -> dict:
             fwd_ms = f0.elapsed_time(f1)
         fit = AdjointMarch(cfg, nsteps, k, precision="fp32", device=dev, stream=stream)
         try:
+            fit.set_launch(launch)
             fit.set_target(D)
             torch.cuda.synchronize(dev)
             a0, a1, a2 = ev(), ev(), ev()
@@ -480,7 +483,7 @@ def bench_large_adjoint(dev, nsteps: int) -> dict:
             fit.close()
     return {"workload": f"1 of 8 beams {n}x{n}, {nsteps} of 3000 steps, checkpoint every {k} (sqrt), FP32, "
                         "6 gains + input field; input field resident on the device",
-            "steps": nsteps, "checkpoint_every": k,
+            "steps": nsteps, "checkpoint_every": k, "launch": launch,
             "forward_march_ms": fwd_ms, "adjoint_forward_ms": afwd_ms, "adjoint_backward_ms": abwd_ms,
             "adjoint_over_forward": (afwd_ms + abwd_ms) / fwd_ms,
             "backward_over_forward": abwd_ms / fwd_ms,

@@ -448,6 +448,14 @@ nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ck
 /* Replace the six screen gains (invalidates a pending forward run). */
 nlse_status nlse_adjoint_set_theta(nlse_adjoint* a, const double* theta);
 
+/* Launch shape of the forward and backward sweeps: a column-tile code and a
+ * row-pass code as for nlse_set_column_tile / nlse_set_row_radix (the radices
+ * change the rounding within the stated tolerances; tiles of one radix and the
+ * staged row pass do not change a bit).  NLSE_EUNSUPPORTED for a code the grid
+ * size or precision does not offer; nothing is changed then.  Invalidates a
+ * pending forward run. */
+nlse_status nlse_adjoint_set_launch(nlse_adjoint* a, int32_t cols, int32_t row_radix);
+
 /* Target fluence D: n x n doubles (host or device), copied in; sum D^2 must be
  * positive (NLSE_EINVAL otherwise).  Synchronises. */
 nlse_status nlse_adjoint_set_target(nlse_adjoint* a, const double* target, int on_device);

@@ -36,6 +36,10 @@ class AdjointMarch:
                                           ptr, self.ws_bytes)
         self._theta = np.array(list(self.params.theta), dtype=np.float64)
 
+    def set_launch(self, launch: dict) -> None:
+        """Column tile and row radix of both sweeps (a tune.tune_launch result)."""
+        capi.nlse_adjoint_set_launch(self.h, int(launch["cols"]), int(launch["row_radix"]))
+
     def set_theta(self, theta) -> None:
         th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(6))
         capi.nlse_adjoint_set_theta(self.h, th.ctypes.data)

@@ -153,6 +153,7 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "nlse_adjoint_set_theta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "nlse_adjoint_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "nlse_adjoint_set_target": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "nlse_adjoint_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double)]),
@@ -335,6 +336,10 @@ def nlse_adjoint_create(p: nlse_params, nsteps: int, ckpt: int, stream: int, wor
                                     ctypes.c_void_p(workspace), ctypes.c_size_t(nbytes), ctypes.byref(h)),
           "nlse_adjoint_create")
     return h
+
+
+def nlse_adjoint_set_launch(h, cols: int, row_radix: int) -> None:
+    check(lib().nlse_adjoint_set_launch(h, int(cols), int(row_radix)), "nlse_adjoint_set_launch")
 
 
 def nlse_adjoint_set_theta(h, theta_ptr: int) -> None:

@@ -1475,6 +1475,21 @@ nlse_status nlse_adjoint_create(const nlse_params* p, int32_t nsteps, int32_t ck
     return NLSE_OK;
 }
 
+nlse_status nlse_adjoint_set_launch(nlse_adjoint* a, int32_t cols, int32_t row_radix) {
+    if (!a) return NLSE_EINVAL;
+    const bool f64 = a->p.precision == NLSE_FP64;
+    const int cmask = f64 ? a->k64->col_mask : a->k32->col_mask;
+    const int rmask = f64 ? a->k64->row_radix_mask : a->k32->row_radix_mask;
+    bool col_ok = false;
+    for (int i = 0; i < kColOptionCount; ++i) col_ok |= kColOptions[i] == cols && ((cmask >> i) & 1);
+    const int bit = row_radix == 16 ? 1 : row_radix == 8 ? 2 : row_radix == (kRowStaged | 16) ? 4 : 0;
+    if (!col_ok || !(rmask & bit)) return NLSE_EUNSUPPORTED;
+    a->cols = cols;
+    a->row_radix = row_radix;
+    a->have_forward = 0;
+    return NLSE_OK;
+}
+
 nlse_status nlse_adjoint_set_theta(nlse_adjoint* a, const double* theta) {
     if (!a || !theta) return NLSE_EINVAL;
     nlse_params q = a->p;

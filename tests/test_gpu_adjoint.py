@@ -108,6 +108,38 @@ def test_checkpoint_spacing_does_not_change_the_gradient():
         assert np.array_equal(g, res[0][2])
 
 
+def test_launch_shape_keeps_the_gradient():
+    """The staged row pass and any staged column tile of radix 16 give the
+    bits of the default launch shape; codes the size does not offer are
+    refused."""
+    from paper_2306_15678_gb300 import capi
+    cfg, U0, D = case(n=2048, nsteps=4, L=4.0, w0=0.5)
+    out = []
+    for launch in ({}, {"cols": capi.NLSE_COL_TMA | 2, "row_radix": capi.NLSE_ROW_STAGED | 16}):
+        fit = AdjointMarch(cfg, 4, 2, precision="fp32")
+        try:
+            if launch:
+                fit.set_launch(launch)
+            fit.set_target(D)
+            J = fit.forward(U0)
+            dth, dU = fit.backward()
+            out.append((J, dth, dU.cpu().numpy()))
+        finally:
+            fit.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    small, U0s, Ds = case()
+    fit = AdjointMarch(small, 4, 2, precision="fp32")
+    try:
+        with pytest.raises(capi.NlseError) as ei:  # n = 64: no staged row pass
+            fit.set_launch({"cols": 1, "row_radix": capi.NLSE_ROW_STAGED | 16})
+        assert ei.value.status == capi.NLSE_EUNSUPPORTED
+        with pytest.raises(capi.NlseError):
+            fit.set_launch({"cols": 3, "row_radix": 16})
+    finally:
+        fit.close()
+
+
 def test_autograd_function_gives_the_adjoint():
     cfg, U0, D = case()
     fit = AdjointMarch(cfg, 20, 5, precision="fp32")
