@@ -365,8 +365,9 @@ nlse_status nlse_destroy(nlse_grid* g);
 typedef struct nlse_batch nlse_batch;
 
 /* Launch shape of the persistent kernel (chosen by an autotuner; see the
- * Python package).  threads: 256 or 512 threads per block (sets the rows and
- * columns per tile); ctas_per_sm: resident blocks per SM (0 = as many as fit);
+ * Python package).  threads: 128, 256 or 512 threads per block (sets the rows
+ * and columns per tile; 128 needs n <= 2048 and radix 16, NLSE_EUNSUPPORTED
+ * otherwise); ctas_per_sm: resident blocks per SM (0 = as many as fit);
  * timeout_ms: bound on every wait; debug_skip_item: test hook -- the work item
  * with this index never reports completion (-1 = none); radix: transform
  * radix of every pass, 16 (or 0: the default; 128 registers per thread) or 8

@@ -447,11 +447,15 @@ template <int THREADS, int E> nlse_status launch_batch(nlse_batch* B, int nsteps
     return cudaGetLastError() == cudaSuccess ? NLSE_OK : NLSE_ECUDA;
 }
 
-// the four launch shapes: threads per block x transform radix
+// the launch shapes: threads per block (128, 256, 512) x transform radix (16, 8;
+// radix 8 at 256 and 512 threads)
 template <typename F> nlse_status with_shape(const nlse_batch_tuning& t, F&& f) {
     if (t.threads == 512)
         return t.radix == 8 ? f(std::integral_constant<int, 512>{}, std::integral_constant<int, 8>{})
                             : f(std::integral_constant<int, 512>{}, std::integral_constant<int, 16>{});
+    if (t.threads == 128)
+        return t.radix == 8 ? NLSE_EUNSUPPORTED
+                            : f(std::integral_constant<int, 128>{}, std::integral_constant<int, 16>{});
     return t.radix == 8 ? f(std::integral_constant<int, 256>{}, std::integral_constant<int, 8>{})
                         : f(std::integral_constant<int, 256>{}, std::integral_constant<int, 16>{});
 }
@@ -516,7 +520,7 @@ nlse_status nlse_batch_create(int32_t count, const nlse_params* params, const nl
     nlse_batch_tuning tn = {256, 0, 2000, -1, 16, 0};
     if (tuning) tn = *tuning;
     if (tn.radix == 0) tn.radix = 16;
-    if (tn.threads != 256 && tn.threads != 512) return NLSE_EINVAL;
+    if (tn.threads != 128 && tn.threads != 256 && tn.threads != 512) return NLSE_EINVAL;
     if (tn.radix != 16 && tn.radix != 8) return NLSE_EINVAL;
     if (tn.ctas_per_sm < 0 || tn.timeout_ms < 1) return NLSE_EINVAL;
     if (tn.per_thread_columns != 0 && tn.per_thread_columns != 1) return NLSE_EINVAL;

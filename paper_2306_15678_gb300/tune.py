@@ -123,14 +123,14 @@ def tune_batch(cfgs: list, steps: int = 10, path: str | None = None, force: bool
     path = path or cache_path()
     cache = _load_cache(path)
     mix = collections.Counter(int(c["n"]) for c in cfgs)
-    key = f"{_gpu_key()}|batch2|" + ",".join(f"{n}x{mix[n]}" for n in sorted(mix))
+    key = f"{_gpu_key()}|batch3|" + ",".join(f"{n}x{mix[n]}" for n in sorted(mix))
     if key in cache and not force:
         return dict(cache[key]["tuning"])
     fields = fields or [beams.make_field(c).astype(np.complex64) for c in cfgs]
     best, timings = None, {}
     for radix in BATCH_RADICES:
-        for threads in (256, 512):
-            for per_sm in (0, 1, 2):
+        for threads in (128, 256, 512):
+            for per_sm in (0, 2):
                 tuning = {"threads": threads, "radix": radix, "ctas_per_sm": per_sm}
                 try:
                     b = Batch(cfgs, tuning)

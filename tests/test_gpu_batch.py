@@ -33,12 +33,13 @@ def single(cfg, U, nsteps, radix=16):
 
 
 @pytest.mark.parametrize("threads,radix,per_thread", [(256, 16, 0), (512, 16, 0), (256, 8, 0), (512, 8, 0),
-                                                      (256, 16, 1), (512, 8, 1)])
+                                                      (128, 16, 0), (256, 16, 1), (512, 8, 1)])
 def test_batched_beams_bit_identical_to_single_grids(threads, radix, per_thread):
     """Every launch shape (threads, radix) and both column paths (staged by
     bulk tensor copies for n >= 512, or per-thread) give each beam the bits of
     the same beam on its own grid with the same radix."""
-    sizes = (256, 512, 1024, 2048, 512, 4096) if threads == 512 or radix == 16 else (256, 512, 1024, 2048, 512)
+    sizes = ((256, 512, 1024, 2048, 512, 4096) if threads == 512 or (threads == 256 and radix == 16)
+             else (256, 512, 1024, 2048, 512))
     cfgs = mixed_beams(sizes)
     fields = [beams.make_field(c).astype(np.complex64) for c in cfgs]
     with Batch(cfgs, {"threads": threads, "radix": radix, "per_thread_columns": per_thread}) as b:
@@ -52,10 +53,14 @@ def test_batched_beams_bit_identical_to_single_grids(threads, radix, per_thread)
             assert np.array_equal(b.field(i, device=True).cpu().numpy(), b.field(i))
 
 
-def test_radix8_batch_rejects_4096_at_256_threads():
+def test_shapes_too_narrow_for_a_size_are_refused():
     cfgs = mixed_beams((4096,))
+    for tuning in ({"threads": 256, "radix": 8}, {"threads": 128, "radix": 16}):
+        with pytest.raises(capi.NlseError) as ei:
+            Batch(cfgs, tuning)
+        assert ei.value.status == capi.NLSE_EUNSUPPORTED
     with pytest.raises(capi.NlseError) as ei:
-        Batch(cfgs, {"threads": 256, "radix": 8})
+        Batch(mixed_beams((512,)), {"threads": 128, "radix": 8})
     assert ei.value.status == capi.NLSE_EUNSUPPORTED
 
 
@@ -127,7 +132,7 @@ def test_autotuner_picks_a_valid_shape(tmp_path):
     from paper_2306_15678_gb300 import tune
     cfgs = mixed_beams((512, 1024))
     t = tune.tune_batch(cfgs, steps=3, path=str(tmp_path / "t.json"))
-    assert t["threads"] in (256, 512) and t["radix"] in (16, 8)
+    assert t["threads"] in (128, 256, 512) and t["radix"] in (16, 8)
     assert tune.tune_batch(cfgs, path=str(tmp_path / "t.json")) == t  # cached
     c = tune.tune_grid(configs.scaled(configs.cfg_dense_fp32(), 1024), "fp32", steps=3,
                        path=str(tmp_path / "t.json"))
