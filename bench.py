@@ -285,6 +285,17 @@ def fp64_ops_per_point_step() -> dict | None:
     return d if d.get("csrc_digest") == csrc_digest(FP64_MARCH_SOURCES) else None
 
 
+def fp32_fma_record() -> dict | None:
+    """FMA-pipe time of the FP32 march kernels at 4096^2 from the ncu capture
+    summarised in profiles/ (valid while the march sources are unchanged)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp32_march_fma.json")) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    return d if d.get("csrc_digest") == csrc_digest() else None
+
+
 def traffic_for(kernel_key: str) -> float | None:
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
@@ -636,6 +647,16 @@ def main():
                     "other_kernel_ms": min(col_avg, row_avg),
                     "step_hbm_frac": (2 * bytes_launch) / (ms / args.steps / 1e3) / 1e9 / peak_gbs,
                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_note}
+        # the FP32 side of the same step: FMA-pipe time at full rate (ncu) over the measured step
+        fma = fp32_fma_record() if n == 4096 else None
+        if fma is not None:
+            fma_us = float(fma["fma_us_per_step_at_full_rate"])
+            roofline["fp32_alu"] = {
+                "bound": "alu", "fma_pipe_us_per_step": fma_us, "step_us": ms / args.steps * 1e3,
+                "frac": fma_us / (ms / args.steps * 1e3),
+                "issue_active": {k: v["issue_active"] for k, v in fma["kernels"].items()},
+                "note": "FMA-pipe busy fraction x duration of one launch of each pass (ncu); the pipe's "
+                        "rate is the same for FP32 and packed FP32x2 (fp64_march.fp32*_fma_peak_per_s)"}
 
         # ---- hot areas (closed regions with fluence >= 0.01 TW/cm^2) of the marched field
         hot = None
