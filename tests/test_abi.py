@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI: the library loads without a GPU, exports every
 function include/nlse.h declares, and validates arguments before any CUDA call."""
+import ctypes
 import os
 import re
 
@@ -154,3 +155,58 @@ def test_exact_screen_validation_on_host():
     assert ei.value.status == capi.NLSE_EUNSUPPORTED
     with pytest.raises(ValueError):
         make_params(dict(cfg, screen="implicit"))
+
+
+def test_ctypes_records_match_the_c_header_layout(tmp_path):
+    """Field offsets and sizes of the ctypes mirrors (nlse_params,
+    nlse_batch_tuning, nlse_lens) equal those gcc computes from
+    include/nlse.h, so every field the binding sets lands where the library
+    reads it."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    records = {"nlse_params": capi.nlse_params, "nlse_batch_tuning": capi.nlse_batch_tuning,
+               "nlse_lens": capi.nlse_lens}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nlse.h"', "int main(void) {"]
+    for name, cls in records.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            rec, field, val = line.split()
+            got[(rec, field)] = int(val)
+    for name, cls in records.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_batch_workspace_size_and_validation_on_host():
+    """Batch sizing needs no GPU: the workspace grows with the beams' fields and
+    their 256 dithered table copies, and sizes or precisions the batched
+    kernel does not take are refused before any CUDA call."""
+    base = configs.cfg_dense_fp32()
+    p512 = make_params(configs.scaled(base, 512), "fp32")
+    p2048 = make_params(configs.scaled(base, 2048), "fp32")
+    one = capi.nlse_batch_workspace_size([p512])
+    two = capi.nlse_batch_workspace_size([p512, p512])
+    mixed = capi.nlse_batch_workspace_size([p512, p2048])
+    assert one >= 512 * 512 * 8 and two > one and mixed > two
+    # the second 512^2 beam adds its field and propagator copies, not another twiddle block
+    assert two - one < 512 * 512 * 8 + 256 * (512 * 8 + 24 * 256) + 4096
+    for bad, status in ((make_params(configs.scaled(base, 128), "fp32"), capi.NLSE_EUNSUPPORTED),
+                        (make_params(configs.scaled(base, 512), "fp64"), capi.NLSE_EUNSUPPORTED)):
+        with pytest.raises(capi.NlseError) as ei:
+            capi.nlse_batch_workspace_size([bad])
+        assert ei.value.status == status
