@@ -752,6 +752,17 @@ def main():
             torch.cuda.synchronize(dev)
             ms64 = a0.elapsed_time(a1)
             v64 = n * n * k64 / (ms64 / 1e3)
+            # the FP32 march over the same 3 + k64 steps against this FP64 march (on the GPU)
+            with Grid(cfg, precision="fp32", diag_every=1, device=dev, stream=stream) as g32:
+                tune.apply_launch(g32, launch)
+                g32.load(U0).step(3 + k64)
+                f32 = g32.fluence(device=True).to(torch.float64)
+                p32 = g32.power()
+            f64 = g64.fluence(device=True)
+            err32 = {"steps": 3 + k64, "fluence_rel_l2": float(torch.linalg.norm(f32 - f64) / torch.linalg.norm(f64)),
+                     "power_rel": abs(p32 / g64.power() - 1),
+                     "tolerance": "fluence rel-L2 <= 2e-4 before the first collapse"}
+            del f32, f64
             g64.close()
             fma64 = alu_peak(1, dev, stream)
             fma32 = alu_peak(0, dev, stream)
@@ -761,7 +772,8 @@ def main():
                     "hbm_frac": 64.0 * v64 / (peak_gbs * 1e9),
                     "fp64_fma_peak_per_s": fma64, "fp32_fma_peak_per_s": fma32,
                     "fp32x2_fma_peak_per_s": fma32x2,
-                    "fp64_over_fp32_fma_rate": fma64 / fma32 if fma32 else None}
+                    "fp64_over_fp32_fma_rate": fma64 / fma32 if fma32 else None,
+                    "fp32_error_vs_fp64": err32}
             if ops and fma64:
                 # FP64 pipe: every DFMA, DMUL and DADD takes one issue slot of the FP64
                 # pipe, which the probe fills with DFMA alone
