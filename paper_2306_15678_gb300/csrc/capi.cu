@@ -351,10 +351,14 @@ void build_tables_f32(const nlse_params* p, HostTables32& t) {
     const size_t poff[4] = {tw32_row_off(n, 16), tw32_row_off(n, 8), tw32_col_off(n, 16), tw32_col_off(n, 8)};
     for (int q = 0; q < 4; ++q)
         for (size_t e = 0; e < pt[q].size() / 2; ++e)
-            for (int c = 0; c < 2; ++c) {  // (wx, wx, wy, wy)
-                float* f = tw + poff[q] / 4 + 4 * e + 2 * c;
-                dither_into(pt[q][2 * e + c], pid[q], e, c, f, cbf);
-                for (int d = 0; d < kDither; ++d) f[(size_t)d * cbf + 1] = f[(size_t)d * cbf];
+            for (int c = 0; c < 2; ++c) {
+                if (q < 2) {  // row tables: (wx, wy)
+                    dither_into(pt[q][2 * e + c], pid[q], e, c, tw + poff[q] / 4 + 2 * e + c, cbf);
+                } else {      // column tables: (wx, wx, wy, wy)
+                    float* f = tw + poff[q] / 4 + 4 * e + 2 * c;
+                    dither_into(pt[q][2 * e + c], pid[q], e, c, f, cbf);
+                    for (int d = 0; d < kDither; ++d) f[(size_t)d * cbf + 1] = f[(size_t)d * cbf];
+                }
             }
 }
 

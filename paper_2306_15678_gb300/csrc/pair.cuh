@@ -32,8 +32,11 @@
 // unevaluated FP32 pairs (hi + lo).  Pass outputs go through one padded
 // shared-memory exchange of 16-byte pairs per pass boundary.
 //
-// Table entries are float4 (wx, wx, wy, wy): the twiddle of both lanes as
-// two packed operands.  The pass of stride NS (NS > 1) owns (R1-1) NS
+// Table entries hold one factor for both lanes, either as float2 (wx, wy),
+// loaded with one 8-byte load and copied into both lanes (less L1 space and
+// traffic, two register moves per operand), or as float4 (wx, wx, wy, wy),
+// loaded as the two packed operands (no moves, more L1); the entry type is the
+// table pointer's.  The pass of stride NS (NS > 1) owns (R1-1) NS
 // entries W_{R1 NS}^{rA k} at (rA-1) NS + k, followed by (R2-1) R1 NS entries
 // W_{R NS}^{i kB} at (i-1) R1 NS + kB.
 #pragma once
@@ -115,14 +118,23 @@ __device__ __forceinline__ C2 cmulw(C2 a, F2 wx, F2 wy, F2 nwy) {
 // swap of the real and imaginary parts (a renaming)
 __device__ __forceinline__ C2 swp(C2 a) { return {a.im, a.re}; }
 
-// twiddle entry (wx, wx, wy, wy) at a compile-time offset (in entries) from a
-// per-pass base, through the read-only path; volatile so that the loads stay
-// where they are used (hoisted, they would hold registers through the passes)
+// twiddle entry at a compile-time offset (in entries) from a per-pass base,
+// through the read-only path, as the packed operands (wx, wx) and (wy, wy);
+// volatile so that the loads stay where they are used (hoisted, they would
+// hold registers through the passes)
+template <int OFF> __device__ __forceinline__ void ldw(const float2* base, F2& wx, F2& wy) {
+    float x, y;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2+%3];" : "=f"(x), "=f"(y) : "l"(base), "n"(OFF * 8));
+    wx = bc(x);
+    wy = bc(y);
+}
 template <int OFF> __device__ __forceinline__ void ldw(const float4* base, F2& wx, F2& wy) {
     asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2+%3];" : "=l"(wx.b), "=l"(wy.b) : "l"(base), "n"(OFF * 16));
 }
-__device__ __forceinline__ void ldw(const float4* p, F2& wx, F2& wy) {
-    asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(wx.b), "=l"(wy.b) : "l"(p));
+// a 16-byte entry holding a different factor per lane, (x0, x1, y0, y1), as
+// the packed operands (x0, x1) and (y0, y1)
+__device__ __forceinline__ void ld_lanes(const float4* p, F2& x, F2& y) {
+    asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(x.b), "=l"(y.b) : "l"(p));
 }
 // one FP32 complex table entry (x, y) through the read-only path
 __device__ __forceinline__ float2 ld1(const float2* p) {
@@ -244,8 +256,8 @@ struct NoHook {
 // runs at the start of the last pass of a transform with more than one pass,
 // when every thread has read the line for the last time: from there on the
 // line is free until the transform returns.
-template <int L, int E, int NS = 1, class H = NoHook>
-__device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __restrict__ tab, int j,
+template <int L, int E, int NS = 1, class H = NoHook, class TE>
+__device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const TE* __restrict__ tab, int j,
                                          const H& hook = H{}) {
     constexpr int REM = L / NS;
     constexpr int R = REM >= E ? E : REM;
@@ -267,7 +279,7 @@ __device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __res
         for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
         // sub-pass A: radix R1 over rA on registers ip + R2 rA, for each ip < R2
         if constexpr (NS > 1 && R1 > 1) {
-            const float4* ta = tab + TA + k;
+            const TE* ta = tab + TA + k;
             sfor<1, R1>([&](auto rc) {
                 constexpr int rA = decltype(rc)::value;
                 F2 wx, wy;
@@ -285,7 +297,7 @@ __device__ __forceinline__ void fft_pair(C2 (&v)[E], C2* sm, const float4* __res
         // sub-pass B: radix R2 over ip on registers ip + R2 jA, for each jA < R1
         if constexpr (R2 > 1) {
             if constexpr (NS > 1) {
-                const float4* tb = tab + TB + k;
+                const TE* tb = tab + TB + k;
                 sfor<0, R1>([&](auto jc) {
                     constexpr int jA = decltype(jc)::value;
                     sfor<1, R2>([&](auto ic) {

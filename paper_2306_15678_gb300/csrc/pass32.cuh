@@ -69,9 +69,9 @@ template <int THREADS, int E> __host__ __device__ constexpr int p_col_min_blocks
 
 // Per-step FP32 twiddle block (one of kDither dithered copies, byte offsets
 // from its start): the single-line table of fft.cuh (n entries of 8 bytes,
-// used by the one-off 2D transforms), the pair tables of the n-point row
-// transform for E = 16 and E = 8, and those of the n/2-point column
-// sub-transforms for E = 16 and E = 8.
+// used by the one-off 2D transforms), the pair tables (8-byte entries) of the
+// n-point row transform for E = 16 and E = 8, and those of the n/2-point
+// column sub-transforms for E = 16 and E = 8.
 //
 // Per-step propagator tables (one of kDitherP dithered copies): P_x, n entries
 // of 8 bytes; P_y, n/2 pair entries of 16 bytes followed by the n/2 cross-lane
@@ -90,15 +90,22 @@ template <int THREADS, int E> __host__ __device__ constexpr int p_col_min_blocks
 constexpr int kDitherP = kDither;
 __host__ __device__ constexpr size_t py32_copy_bytes(int n) { return (size_t)16 * (n / 2) + (size_t)8 * (n / 2); }
 __host__ __device__ constexpr int tw32_min(int a, int b) { return a < b ? a : b; }
+// Pair-table entry formats (pair.cuh): 8-byte (wx, wy) for the row transforms
+// (half the L1 footprint and traffic of the tables: row pass 111 -> 103 us at
+// 4096^2), 16-byte (wx, wx, wy, wy) for the column transforms, whose kernel
+// has no registers left for the copies into both lanes (8-byte entries there:
+// 90 -> 112 us, with spills).
+using RowTab = float2;
+using ColTab = float4;
 __host__ __device__ constexpr size_t tw32_row_off(int n, int e) {
-    return (size_t)8 * n + (e >= 16 ? 0 : (size_t)16 * pr::pair_tab_entries(n, tw32_min(16, n)));
+    return (size_t)8 * n + (e >= 16 ? 0 : sizeof(RowTab) * pr::pair_tab_entries(n, tw32_min(16, n)));
 }
 __host__ __device__ constexpr size_t tw32_col_off(int n, int e) {
-    return tw32_row_off(n, 8) + (size_t)16 * pr::pair_tab_entries(n, tw32_min(8, n)) +
-           (e >= 16 ? 0 : (size_t)16 * pr::pair_tab_entries(n / 2, tw32_min(16, n / 2)));
+    return tw32_row_off(n, 8) + sizeof(RowTab) * pr::pair_tab_entries(n, tw32_min(8, n)) +
+           (e >= 16 ? 0 : sizeof(ColTab) * pr::pair_tab_entries(n / 2, tw32_min(16, n / 2)));
 }
 __host__ __device__ constexpr size_t tw32_copy_bytes(int n) {
-    return (tw32_col_off(n, 8) + (size_t)16 * pr::pair_tab_entries(n / 2, tw32_min(8, n / 2)) + 255) / 256 * 256;
+    return (tw32_col_off(n, 8) + sizeof(ColTab) * pr::pair_tab_entries(n / 2, tw32_min(8, n / 2)) + 255) / 256 * 256;
 }
 
 // Global-memory access of the units: plain for the per-pass kernels, L2-only
@@ -243,7 +250,7 @@ __device__ __forceinline__ C2 apply_screen2(C2 v, const ScreenCoef<float>& c, un
 // first screen); EXACT compiles the exact pointwise substep in.  hook runs in
 // the forward transform once the line is free (pair.cuh: fft_pair).
 template <int N, int ER, bool DIAG, bool EXACT = true, class H = pr::NoHook>
-__device__ __forceinline__ void row_body32(C2 (&v)[p_e<N, ER>()], C2* sm, const float4* __restrict__ tab,
+__device__ __forceinline__ void row_body32(C2 (&v)[p_e<N, ER>()], C2* sm, const RowTab* __restrict__ tab,
                                            const ScreenCoef<float>& sc, int j, float& tsum, float& tmax,
                                            const H& hook = H{}) {
     constexpr int E = p_e<N, ER>();
@@ -311,7 +318,7 @@ __device__ __forceinline__ void row_tile32(const float4* src, float4* dst, const
     const int g = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
     const size_t row = (size_t)(pair0 + g) * N;
     C2* sm = smem + g * LS;
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, ER));
+    const RowTab* tab = reinterpret_cast<const RowTab*>(twb + tw32_row_off(N, ER));
     C2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = pr::swp(M::ld(src + row + j + m * T));  // B_x = swap F_x swap
@@ -345,7 +352,7 @@ __device__ __forceinline__ void col_body32(C2 (&v)[p_e<N / 2, EC>()], C2* sm, co
                                            const float2* __restrict__ px, const float4* __restrict__ py,
                                            float2 rot, int col, int j) {
     constexpr int L = N / 2, E = p_e<L, EC>(), T = p_tpl<L, EC>();
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_col_off(N, EC));
+    const ColTab* tab = reinterpret_cast<const ColTab*>(twb + tw32_col_off(N, EC));
     const float2* cross = reinterpret_cast<const float2*>(py + L);  // after the n/2 P_y entries
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
@@ -373,7 +380,7 @@ __device__ __forceinline__ void col_body32(C2 (&v)[p_e<N / 2, EC>()], C2* sm, co
                 X = pr::cmulw(X, qx, qy, nqy);
                 X = {pr::fma(X.re, xd, pr::fma(X.im, nxs, X.re)), pr::fma(X.im, xd, pr::fma(X.re, xs, X.im))};
                 F2 yd, ys;
-                pr::ldw(py + k, yd, ys);
+                pr::ld_lanes(py + k, yd, ys);
                 X = {pr::fma(X.re, yd, pr::fma(X.im, pr::neg(ys), X.re)), pr::fma(X.im, yd, pr::fma(X.re, ys, X.im))};
                 // Y = swap(X): A = Y[k] + Y[k + L], B = (Y[k] - Y[k + L]) W_n^k
                 float yr0, yr1, yi0, yi1;
@@ -459,7 +466,7 @@ k_row_pass32_pf(const float4* src, float4* dst, const unsigned char* twb, Screen
     __shared__ uint64_t bar;
     __shared__ int s_fail;
     C2* line = reinterpret_cast<C2*>(smraw);
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, 16));
+    const RowTab* tab = reinterpret_cast<const RowTab*>(twb + tw32_row_off(N, 16));
     const int j = (int)threadIdx.x;
     pdl_trigger();
     pdl_wait();
@@ -609,7 +616,7 @@ k_row_forward32(const float2* __restrict__ src, float4* __restrict__ dst, const 
     extern __shared__ __align__(16) unsigned char smraw[];
     const int g = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
     const size_t p = (size_t)blockIdx.x * RP + g;
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, 16));
+    const RowTab* tab = reinterpret_cast<const RowTab*>(twb + tw32_row_off(N, 16));
     C2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -633,7 +640,7 @@ k_readout32(const float4* __restrict__ state, const unsigned char* twb, float2* 
     extern __shared__ __align__(16) unsigned char smraw[];
     const int g = (int)threadIdx.x / T, j = (int)threadIdx.x % T;
     const size_t p = (size_t)blockIdx.x * RP + g;
-    const float4* tab = reinterpret_cast<const float4*>(twb + tw32_row_off(N, 16));
+    const RowTab* tab = reinterpret_cast<const RowTab*>(twb + tw32_row_off(N, 16));
     C2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = pr::swp(UnitPlain::ld(state + p * N + j + m * T));
