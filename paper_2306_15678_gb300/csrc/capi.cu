@@ -378,6 +378,7 @@ struct nlse_grid {
     int cols;  // column tile of the column pass
     int row_radix;  // radix of the row pass (FP32: 16 or 8)
     unsigned debug_extra_tx;  // test hook of the staged column pass (NLSE_DEBUG_COL_EXTRA_TX), 0 in use
+    unsigned debug_row_extra_tx;  // test hook of the staged row pass (NLSE_DEBUG_ROW_EXTRA_TX), 0 in use
     double theta;  // accumulated global phase of the stored field, mod 2 pi
     const KernelSet<float>* k32;
     const KernelSet<double>* k64;
@@ -504,8 +505,8 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
             sc.reps = 1;
             sc.scale = (T)1 / (T)n;
             if (ks->row_pass(field, field, twiddles_at<T>(g->ws + g->lay.tw, n, k), sc, partials, false,
-                             g->row_radix, reinterpret_cast<int*>(g->ws + g->lay.status), g->stream) !=
-                cudaSuccess)
+                             g->row_radix, reinterpret_cast<int*>(g->ws + g->lay.status), g->debug_row_extra_tx,
+                             g->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             sc.scale = (T)1;
         }
@@ -525,7 +526,7 @@ template <typename T> nlse_status step_impl(nlse_grid* g, int nsteps, cudaEvent_
         double* slot = dat(g, g->lay.diag) + 2 * (size_t)g->diag_pending * row_parts(ks, g->row_radix);
         sc.reps = strang && s + 1 < nsteps ? 2 : 1;
         e = ks->row_pass(field, field, tw, sc, diag ? slot : partials, diag, g->row_radix,
-                         reinterpret_cast<int*>(g->ws + g->lay.status), g->stream);
+                         reinterpret_cast<int*>(g->ws + g->lay.status), g->debug_row_extra_tx, g->stream);
         if (e != cudaSuccess) return NLSE_ECUDA;
         if (diag && ++g->diag_pending == kDiagBatch && flush_diag<T>(g) != NLSE_OK) return NLSE_ECUDA;
         if (ev && cudaEventRecord(ev[2 * s + 2], g->stream) != cudaSuccess) return NLSE_ECUDA;
@@ -818,6 +819,7 @@ nlse_status nlse_create(const nlse_params* p, void* cuda_stream, void* dev_works
         g->sc32 = screen_coef<float>(&screen_p);
     }
     if (const char* env = std::getenv("NLSE_DEBUG_COL_EXTRA_TX")) g->debug_extra_tx = (unsigned)std::atoi(env);
+    if (const char* env = std::getenv("NLSE_DEBUG_ROW_EXTRA_TX")) g->debug_row_extra_tx = (unsigned)std::atoi(env);
     if (const char* env = std::getenv("NLSE_COL_TILE")) {
         const int c = std::atoi(env);
         const int mask = p->precision == NLSE_FP64 ? g->k64->col_mask : g->k32->col_mask;
@@ -1351,7 +1353,8 @@ template <typename T> nlse_status adj_forward_impl(nlse_adjoint* a, const void* 
                          py_at<T>(a->ws + a->lay.py, n, s), rot_for_step<T>(s, nullptr), a->cols, nullptr,
                          0u, a->stream) != cudaSuccess)
             return NLSE_ECUDA;
-        if (ks->row_pass(state, state, tws, sc, partials, false, a->row_radix, nullptr, a->stream) != cudaSuccess)
+        if (ks->row_pass(state, state, tws, sc, partials, false, a->row_radix, nullptr, 0u, a->stream) !=
+            cudaSuccess)
             return NLSE_ECUDA;
     }
     double* result = reinterpret_cast<double*>(a->ws + a->lay.result);
@@ -1394,7 +1397,7 @@ template <typename T> nlse_status adj_backward_impl(nlse_adjoint* a, double* dth
                              nullptr, 0u, a->stream) != cudaSuccess)
                 return NLSE_ECUDA;
             if (s + 1 < c1 &&
-                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->row_radix, nullptr, a->stream) !=
+                ks->row_pass(seg(s - c0), state, tws, ac.sc, partials, false, a->row_radix, nullptr, 0u, a->stream) !=
                     cudaSuccess)
                 return NLSE_ECUDA;
         }

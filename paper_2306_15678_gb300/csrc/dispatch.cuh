@@ -42,9 +42,10 @@ template <typename T> struct KernelSet {
                             // bit 2: radix 16 with staged persistent blocks (kRowStaged | 16)
     int row_radix_default;  // default radix of the row pass (16 or 8)
     // rad: row-pass code (16, 8 or kRowStaged | 16; FP64: 8); status: device
-    // status word (bit 1: a bounded wait ran out), may be null
+    // status word (bit 1: a bounded wait ran out), may be null; extra_tx: test
+    // hook of the staged variant (0 in use)
     cudaError_t (*row_pass)(const V* src, V* dst, const W* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, int rad, int* status, cudaStream_t s);
+                            bool diag, int rad, int* status, unsigned extra_tx, cudaStream_t s);
     // status: device status word (bit 1: a bounded wait ran out), may be null;
     // extra_tx: test hook of the staged variant (0 in use)
     cudaError_t (*col_pass)(const V* src, V* dst, const W* tw, const W* px, const W* py, W rot,
@@ -133,7 +134,7 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, int smem, cu
 template <typename T, int N>
 cudaError_t launch_row_pass(const typename vec2<T>::type* src, typename vec2<T>::type* dst,
                             const typename tab_of<T>::type* tw, ScreenCoef<T> sc, double* partials,
-                            bool diag, int, int*, cudaStream_t s) {
+                            bool diag, int, int*, unsigned, cudaStream_t s) {
     constexpr int RPB = rows_per_block<T, N>(), THREADS = threads_per_line<T, N>() * RPB;
     constexpr int SMEM = row_smem_bytes<T, N>();
     cudaError_t e;

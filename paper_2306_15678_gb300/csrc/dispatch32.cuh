@@ -54,7 +54,7 @@ inline int resident_grid(int per_sm, int units) {
 
 template <int N>
 cudaError_t launch_row_pass32_pf(const float2* src, float2* dst, const float2* tw, ScreenCoef<float> sc,
-                                 double* partials, bool diag, int* status, cudaStream_t s) {
+                                 double* partials, bool diag, int* status, unsigned extra_tx, cudaStream_t s) {
     if constexpr (p_row_staged_ok<N>()) {
         constexpr int THREADS = p_tpl<N, 16>(), SMEM = p_row_smem<N, 16>();
         constexpr int RES = p_min_blocks<THREADS, 16>();
@@ -65,11 +65,11 @@ cudaError_t launch_row_pass32_pf(const float2* src, float2* dst, const float2* t
         if (diag) {
             if ((e = ensure_smem_carveout<k_row_pass32_pf<N, true>>(SMEM, RES)) != cudaSuccess) return e;
             e = launch_pdl(k_row_pass32_pf<N, true>, dim3(grid), dim3(THREADS), SMEM, s, in, out, twb_of(tw), sc,
-                           partials, status);
+                           partials, status, extra_tx);
         } else {
             if ((e = ensure_smem_carveout<k_row_pass32_pf<N, false>>(SMEM, RES)) != cudaSuccess) return e;
             e = launch_pdl(k_row_pass32_pf<N, false>, dim3(grid), dim3(THREADS), SMEM, s, in, out, twb_of(tw), sc,
-                           partials, status);
+                           partials, status, extra_tx);
         }
         return e != cudaSuccess ? e : cudaGetLastError();
     } else {
@@ -79,10 +79,11 @@ cudaError_t launch_row_pass32_pf(const float2* src, float2* dst, const float2* t
 
 template <int N>
 cudaError_t launch_row_pass32(const float2* src, float2* dst, const float2* tw, ScreenCoef<float> sc,
-                              double* partials, bool diag, int rad, int* status, cudaStream_t s) {
+                              double* partials, bool diag, int rad, int* status, unsigned extra_tx, cudaStream_t s) {
     if (rad == 16) return launch_row_pass32_e<N, 16>(src, dst, tw, sc, partials, diag, s);
     if (rad == 8) return launch_row_pass32_e<N, 8>(src, dst, tw, sc, partials, diag, s);
-    if (rad == (kRowStaged | 16)) return launch_row_pass32_pf<N>(src, dst, tw, sc, partials, diag, status, s);
+    if (rad == (kRowStaged | 16))
+        return launch_row_pass32_pf<N>(src, dst, tw, sc, partials, diag, status, extra_tx, s);
     return cudaErrorInvalidConfiguration;
 }
 

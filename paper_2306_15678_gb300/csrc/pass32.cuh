@@ -415,9 +415,11 @@ k_row_pass32(const float4* src, float4* dst, const unsigned char* twb, ScreenCoe
 
 // One contiguous bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
 // aligned) from global into shared memory, counted in bytes on bar; the calling
-// thread also arms bar for those bytes.
-__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    mbar_expect_tx(bar, bytes);
+// thread also arrives on bar, expecting those bytes (plus `extra`, a test hook
+// that keeps the phase from completing).
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint32_t extra = 0) {
+    mbar_expect_tx(bar, bytes + extra);
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
@@ -454,11 +456,13 @@ __device__ __forceinline__ void block_partials32_at(float tsum, float tmax, doub
 // the last transform pass, the stores and the partials of the current row
 // pair run.  Arithmetic, stores and partials (one slot per row pair) are those
 // of k_row_pass32 at radix 16, bit for bit.  The wait for a copy is bounded as
-// in the staged column pass (status bits 2 and 4, tma.cuh).
+// in the staged column pass (status bits 2 and 4, tma.cuh).  extra_tx (a test
+// hook, 0 in use) makes block 0 expect that many bytes more for its first row
+// pair than the copy brings, so that its wait runs out.
 template <int N, bool DIAG>
 __global__ void __launch_bounds__(p_tpl<N, 16>(), p_min_blocks<p_tpl<N, 16>(), 16>())
 k_row_pass32_pf(const float4* src, float4* dst, const unsigned char* twb, ScreenCoef<float> sc,
-                double* __restrict__ partials, int* __restrict__ status) {
+                double* __restrict__ partials, int* __restrict__ status, uint32_t extra_tx) {
     constexpr int E = p_e<N, 16>(), T = p_tpl<N, 16>(), NP = N / 2;
     constexpr uint32_t BYTES = (uint32_t)N * 16;
     static_assert(p_rows<N, 16>() == 1 && T % 32 == 0, "one row pair of whole warps per block");
@@ -473,7 +477,8 @@ k_row_pass32_pf(const float4* src, float4* dst, const unsigned char* twb, Screen
     if (threadIdx.x == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
-        if ((int)blockIdx.x < NP) bulk_load_1d(line, src + (size_t)blockIdx.x * N, BYTES, &bar);
+        if ((int)blockIdx.x < NP)
+            bulk_load_1d(line, src + (size_t)blockIdx.x * N, BYTES, &bar, blockIdx.x == 0 ? extra_tx : 0u);
     }
     __syncthreads();
     uint32_t parity = 0;

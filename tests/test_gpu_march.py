@@ -169,6 +169,30 @@ def test_staged_column_pass_wait_runs_out_cleanly(monkeypatch):
     assert rel_l2(U, ref) < 1e-5
 
 
+def test_staged_row_pass_wait_runs_out_cleanly(monkeypatch):
+    """Block 0 of the staged (persistent) row pass is made to expect 16 bytes
+    more than its first bulk copy brings: its bounded waits run out (1 s
+    each), the grid reports NLSE_ETIMEOUT, and the context stays usable: the
+    next grid's staged row pass gives the bits of the radix-16 row pass."""
+    cfg = configs.scaled(configs.cfg_dense_fp32(), 2048, nsteps=3)
+    U0 = beams.make_field(cfg).astype(np.complex64)
+    monkeypatch.setenv("NLSE_DEBUG_ROW_EXTRA_TX", "16")
+    with Grid(cfg, precision="fp32") as g:
+        capi.nlse_set_row_radix(g.h, capi.NLSE_ROW_STAGED | 16)
+        g.load(U0).step(1)
+        torch.cuda.synchronize()
+        assert g.device_status() == capi.NLSE_ETIMEOUT
+        assert g.device_status() == capi.NLSE_OK  # reading clears the word
+    monkeypatch.delenv("NLSE_DEBUG_ROW_EXTRA_TX")
+    out = []
+    for r in (capi.NLSE_ROW_STAGED | 16, 16):
+        with Grid(cfg, precision="fp32") as g:
+            capi.nlse_set_row_radix(g.h, r)
+            out.append(g.load(U0).step(3).field())
+            assert g.device_status() == capi.NLSE_OK
+    assert np.array_equal(out[0], out[1])
+
+
 # ------------------------------------------------------------ plain FP64
 
 def test_plain_fp64_256_matches_oracle():
